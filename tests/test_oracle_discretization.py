@@ -1,0 +1,255 @@
+"""Pins of the oracle's discretisation (paper Sect. 2) against what the
+mathematics fixes: consistency with the PDEs at second order, telescoping
+conservation, preserved equilibria, and the linear sound speed (Sect. 3.3.1)."""
+import math
+
+import numpy as np
+import pytest
+import sympy as sp
+import torch
+
+import workloads as W
+from oracle import discretization as D
+from oracle import jfnk as J
+
+# ---------------------------------------------------------------------------
+# consistency with Eqs. cons1-cons3 / Etot at second order
+# ---------------------------------------------------------------------------
+
+_x, _y, _z = sp.symbols("x y z")
+
+
+def _exact_rhs(fields, gamma, g, K0, form, ndim):
+    """Continuous right-hand sides of Eqs. cons1-cons3 (form 0) or cons1,
+    Etot, cons3 (form 1) for analytic fields, derived with sympy."""
+    coords = [_x, _y, _z][:ndim]
+    rho, e = fields[0], fields[1]
+    u = fields[2:2 + ndim]
+    p = (gamma - 1) * rho * e
+    T = (gamma - 1) * e
+    chi = K0 * T ** 3
+    div = lambda vec: sum(sp.diff(vec[d], coords[d]) for d in range(ndim))      # noqa: E731
+    cond = sum(sp.diff(chi * sp.diff(T, c), c) for c in coords)
+    R_rho = -div([rho * u[d] for d in range(ndim)])
+    if form == 0:
+        R_E = -div([rho * e * u[d] for d in range(ndim)]) - p * div(u) + cond
+    else:
+        eps = e + sum(ud * ud for ud in u) / 2
+        R_E = -div([(rho * eps + p) * u[d] for d in range(ndim)]) + \
+            rho * sum(u[d] * g[d] for d in range(ndim)) + cond
+    R_mom = [-div([rho * u[c] * u[d] for d in range(ndim)]) - sp.diff(p, coords[c]) + rho * g[c]
+             for c in range(ndim)]
+    E = e if form == 0 else e + sum(ud * ud for ud in u) / 2
+    return E, [R_rho, R_E] + R_mom
+
+
+def _sample(expr, n, h, ndim, stagger):
+    """Point values of expr at cell centres, shifted down by h/2 along
+    direction `stagger` (face positions) if stagger >= 0."""
+    f = sp.lambdify([_x, _y, _z][:ndim], expr, "numpy")
+    grids = []
+    for d in range(ndim):
+        c = (np.arange(n) + 0.5) * h
+        if d == stagger:
+            c = c - 0.5 * h
+        grids.append(c)
+    mesh = np.meshgrid(*grids[::-1], indexing="ij")[::-1]
+    out = np.asarray(f(*mesh), dtype=np.float64) + np.zeros(mesh[0].shape)
+    if ndim == 2:
+        out = out[None]
+    return out
+
+
+def _consistency_errors(fields_expr, ndim, form, bc, ns, gamma=5 / 3, g=(0.3, -0.7, 0.4), K0=0.05):
+    g = g[:ndim]
+    E, rhs_ex = _exact_rhs(fields_expr, gamma, g, K0, form, ndim)
+    errs = []
+    for n in ns:
+        h = 1.0 / n
+        samp = [_sample(fields_expr[0], n, h, ndim, -1), _sample(E, n, h, ndim, -1)]
+        samp += [_sample(fields_expr[2 + c], n, h, ndim, c) for c in range(ndim)]
+        X = np.concatenate([a.ravel() for a in samp])
+        nn = (n, n, n if ndim == 3 else 1)
+        P = D.Problem(ndim=ndim, n=nn, dx=(h, h, h if ndim == 3 else 1.0), bc=tuple(bc) + (0,) * (3 - len(bc)),
+                      gamma=gamma, g=tuple(g) + (0.0,) * (3 - ndim), K0=K0, chi_exp=3.0, energy_form=form,
+                      theta=0.5)
+        R = D.rhs(P, X)
+        ex = [_sample(rhs_ex[0], n, h, ndim, -1), _sample(rhs_ex[1], n, h, ndim, -1)]
+        ex += [_sample(rhs_ex[2 + c], n, h, ndim, c) for c in range(ndim)]
+        row = []
+        for k in range(2 + ndim):
+            a = R[k].numpy()
+            b = ex[k]
+            if k >= 2 and bc[k - 2] == W.BC_WALL:
+                sl = [slice(None)] * 3
+                sl[2 - (k - 2)] = slice(1, None)          # unknown faces only
+                a, b = a[tuple(sl)], b[tuple(sl)]
+            row.append(float(np.mean(np.abs(a - b)) / np.mean(np.abs(b))))
+        errs.append(row)
+    return np.array(errs)
+
+
+def _periodic_fields_2d():
+    pi = sp.pi
+    x, y = _x, _y
+    rho = 1 + sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(2 * pi * y)
+    e = 2 + sp.Rational(3, 10) * sp.cos(2 * pi * x + sp.Rational(1, 2)) * sp.sin(2 * pi * y)
+    u = sp.Rational(3, 10) + sp.Rational(1, 5) * sp.sin(2 * pi * (x + y))
+    v = -sp.Rational(1, 5) + sp.Rational(1, 10) * sp.cos(2 * pi * x)
+    return [rho, e, u, v]
+
+
+@pytest.mark.parametrize("form", [D.ENERGY_INTERNAL, D.ENERGY_TOTAL])
+def test_second_order_consistency_2d_periodic(form):
+    errs = _consistency_errors(_periodic_fields_2d(), 2, form, (0, 0), (32, 64, 128))
+    ratios = errs[:-1] / errs[1:]
+    assert np.all(errs[-1] < 1e-3), errs
+    assert np.all(ratios[-1] > 3.3), ratios          # order > 1.7 in every equation
+
+
+def test_second_order_consistency_2d_walls():
+    """Walls in y: fields even about the walls, v odd, so the mirror ghosts
+    are exact and the boundary rows must converge like the interior."""
+    pi = sp.pi
+    x, y = _x, _y
+    rho = 1 + sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(2 * pi * y)
+    e = 2 + sp.Rational(3, 10) * sp.cos(2 * pi * x + sp.Rational(1, 2)) * sp.cos(2 * pi * y)
+    u = sp.Rational(3, 10) + sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(2 * pi * y)
+    v = sp.Rational(1, 10) * sp.sin(2 * pi * y) * (1 + sp.Rational(1, 2) * sp.cos(2 * pi * x))
+    errs = _consistency_errors([rho, e, u, v], 2, D.ENERGY_INTERNAL, (0, 1), (32, 64, 128), g=(0.0, -0.7, 0.0))
+    ratios = errs[:-1] / errs[1:]
+    assert np.all(ratios[-1] > 3.0), (errs, ratios)
+
+
+def test_second_order_consistency_3d():
+    pi = sp.pi
+    x, y, z = _x, _y, _z
+    rho = 1 + sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(2 * pi * (y + z))
+    e = 2 + sp.Rational(3, 10) * sp.cos(2 * pi * x + sp.Rational(1, 2)) * sp.sin(2 * pi * z)
+    u = sp.Rational(3, 10) + sp.Rational(1, 5) * sp.sin(2 * pi * (x + y))
+    v = -sp.Rational(1, 5) + sp.Rational(1, 10) * sp.cos(2 * pi * (x - z))
+    w = sp.Rational(1, 10) + sp.Rational(1, 10) * sp.sin(2 * pi * y)
+    errs = _consistency_errors([rho, e, u, v, w], 3, D.ENERGY_TOTAL, (0, 0, 0), (16, 32))
+    ratios = errs[0] / errs[1]
+    assert np.all(ratios > 3.0), (errs, ratios)
+
+
+# ---------------------------------------------------------------------------
+# conservation, equilibria
+# ---------------------------------------------------------------------------
+
+def _problem(wl, **kw):
+    P = D.Problem.from_workload(wl)
+    for k, v in kw.items():
+        setattr(P, k, v)
+    return P
+
+
+@pytest.mark.parametrize("form", [D.ENERGY_INTERNAL, D.ENERGY_TOTAL])
+def test_flux_form_telescopes_periodic(form):
+    """Without gravity, sum R_rho = sum R_rho u = 0 (and sum R_rho eps_t = 0
+    for the total-energy form) on a random periodic state."""
+    wl = W.config(3, n=(8, 8, 8), mach=0.5)
+    P = _problem(wl, energy_form=form, K0=0.07)
+    X = W.random_state(wl, 11, rel=0.3, vel=0.5)
+    R = D.rhs(P, X)
+    U = D.conserved(P, X)
+    for k in [0] + ([1] if form == D.ENERGY_TOTAL else []) + [2, 3, 4]:
+        scale = float(torch.sum(torch.abs(U[k]))) * 1e3 + float(torch.sum(torch.abs(R[k])))
+        assert abs(float(R[k].sum())) < 1e-13 * scale, (k, float(R[k].sum()))
+    if form == D.ENERGY_INTERNAL:
+        # the -p div u source makes the internal energy sum non-zero
+        assert abs(float(R[1].sum())) > 1e-6 * float(torch.sum(torch.abs(R[1])))
+
+
+def test_flux_form_telescopes_walls():
+    """Walls carry no flux: mass, total energy and the momentum parallel to
+    the walls are conserved in a box with walls in z (no gravity)."""
+    wl = W.config(4, n=(8, 8, 8))
+    P = _problem(wl, energy_form=D.ENERGY_TOTAL, g=(0.0, 0.0, 0.0))
+    X = W.random_state(wl, 12, rel=0.3, vel=0.5)
+    R = D.rhs(P, X)
+    for k in (0, 1, 2, 3):
+        scale = float(torch.sum(torch.abs(R[k])))
+        assert abs(float(R[k].sum())) < 1e-13 * scale * 100, k
+
+
+def test_uniform_state_is_steady():
+    wl = W.config(3, n=(8, 8, 8))
+    P = _problem(wl, K0=0.3)
+    f = [np.full(P.shape, v) for v in (1.3, 2.1, 0.4, -0.2, 0.1)]
+    X = np.concatenate([a.ravel() for a in f])
+    R = D.rhs(P, X)
+    for k in range(5):
+        assert float(torch.max(torch.abs(R[k]))) < 1e-14 * 10
+
+
+@pytest.mark.parametrize("cid,n", [(2, (32, 32)), (4, (8, 8, 8))])
+def test_discrete_hydrostatic_equilibrium(cid, n):
+    """A polytrope built from the discrete face balance is an exact steady
+    state of the residual (no conduction): F = 0 to round-off."""
+    wl = W.make_stratified(n if len(n) == 3 else (n[0], n[1], 1), len(n), seed=1, cfl=10.0, n_steps=1,
+                           n_poly=1.5 if cid == 2 else 1.4, contrast=10.0 if cid == 2 else 20.0,
+                           blobs=0, vel_noise_mach=0.0)
+    P = _problem(wl, K0=0.0)
+    R = D.rhs(P, wl.X0)
+    f = wl.fields()
+    pscale = float(np.max((wl.gamma - 1) * f[0] * f[1])) / min(wl.dx[:wl.ndim])
+    for k in range(2 + wl.ndim):
+        assert float(torch.max(torch.abs(R[k]))) < 1e-13 * pscale, k
+    # with conduction the same state is not steady in energy only
+    P2 = _problem(wl)
+    R2 = D.rhs(P2, wl.X0)
+    assert float(torch.max(torch.abs(R2[1]))) > 1e-6
+    assert float(torch.max(torch.abs(R2[2 + wl.ndim - 1]))) < 1e-13 * pscale
+
+
+def test_hydrostatic_state_survives_a_step():
+    wl = W.make_stratified((16, 16, 1), 2, seed=1, cfl=50.0, n_steps=1, n_poly=1.5, contrast=10.0,
+                           blobs=0, vel_noise_mach=0.0)
+    P = _problem(wl, K0=0.0)
+    dt = D.cfl_dt(P, wl.X0, 50.0)
+    X1, st = J.newton_step(P, wl.X0, dt, J.Options(precond=1))
+    assert st.converged
+    rel = float(torch.max(torch.abs(X1 - torch.as_tensor(wl.X0))[: 2 * P.ncell] /
+                          torch.as_tensor(wl.X0)[: 2 * P.ncell]))
+    assert rel < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# linear sound speed a = sqrt(Gamma1 p0 / rho0) (Sect. 3.3.1)
+# ---------------------------------------------------------------------------
+
+def test_linear_sound_speed():
+    """A right-going plane acoustic wave returns to its start after one
+    period L/a (Crank-Nicolson, CFL_hydro = 1): phase error < 1 % of a
+    period and amplitude kept within 2 %."""
+    nx, ny = 32, 4
+    gamma, rho0, p0, eps = 5 / 3, 1.0, 1.0, 1e-6
+    a = math.sqrt(gamma * p0 / rho0)
+    h = 1.0 / nx
+    xc = (np.arange(nx) + 0.5) * h
+    xf = np.arange(nx) * h
+    k = 2 * math.pi
+    pp = eps * p0 * np.sin(k * xc)
+    p = p0 + pp
+    rho = rho0 + pp / a ** 2
+    e = p / ((gamma - 1) * rho)
+    u = eps * p0 * np.sin(k * xf) / (rho0 * a)
+    shape = (1, ny, nx)
+    fields = [np.broadcast_to(rho, shape), np.broadcast_to(e, shape), np.broadcast_to(u, shape), np.zeros(shape)]
+    X = torch.as_tensor(np.concatenate([np.ascontiguousarray(f).ravel() for f in fields]))
+    P = D.Problem(ndim=2, n=(nx, ny, 1), dx=(h, 1.0 / ny, 1.0), bc=(0, 0, 0), gamma=gamma, g=(0, 0, 0),
+                  K0=0.0, chi_exp=3.0, energy_form=0, theta=0.5)
+    steps = 32
+    dt = (1.0 / a) / steps                                   # CFL_hydro = a dt / h = 1
+    opts = J.Options(precond=1, eta=1e-10, newton_tol=1e-13, gmres_m=40)
+    for _ in range(steps):
+        X, st = J.newton_step(P, X, dt, opts)
+    f = D.unpack(P, X)
+    pf = ((gamma - 1) * f[0] * f[1])[0, 0].numpy() - p0
+    s, c = np.sum(pf * np.sin(k * xc)), np.sum(pf * np.cos(k * xc))
+    phase = math.atan2(c, s)                                # 0 when back in place
+    amp = math.hypot(s, c) / np.sum((eps * p0 * np.sin(k * xc)) ** 2) * eps * p0
+    assert abs(phase) / (2 * math.pi) < 0.01, phase
+    assert abs(amp - 1.0) < 0.02, amp
