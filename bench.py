@@ -1,0 +1,397 @@
+"""Benchmark: implicit JFNK steps on the 3D stratified convective box.
+
+Workload: problem 4 of `workloads` -- 256^3 cells, walls in z, gravity along
+-z, superadiabatic polytrope (index 1.4, density contrast 20), conduction
+chi = K0 T^3, seeded velocity noise (rms Mach 1e-3), CFL_hydro = 200,
+Crank-Nicolson, sound + conduction physics-based preconditioner, Newton
+tolerance 1e-8, GMRES(30) with eta = 1e-4.  A "step" is one implicit time
+step (all Newton iterations, each with its GMRES solve: preconditioner
+applies, Jacobian-free products, Gram-Schmidt).  The state (670 MB per FP64
+vector) is far larger than L2, so no flush is needed between steps.
+
+Arms: the default arm times the CUDA library in mixed precision (FP32 Krylov
+basis and preconditioner, FP64 residual) -- `value` -- and the plain FP64
+path beside it.  `--impl reference` times the CPU oracle (the only reference
+implementation of the paper's method here) on the host cores.
+
+Multi-GPU: the method as built runs on one GPU; with torchrun each rank runs
+an independent replica (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "implicit steps/s & Jv Gcell/s at 256³: FP32-Krylov vs FP64 plain, Newton tol 1e-8"
+UNIT = "implicit steps/s"
+NEWTON_TOL = 1e-8
+ETA = 1e-4
+
+# Executed FP64 floating-point operations per cell of one residual evaluation
+# inside Jv, per kernel (3D, internal energy, gravity, conduction), from the
+# ncu instruction counters (dadd + dmul + 2 dfma) of a 64^3 capture divided
+# by the cell count; division and square-root sequences are included as the
+# DFMA/DMUL/DADD instructions they execute.  See profiles/.
+FP64_FLOPS_PER_CELL = {"perturb": 10.0, "eos": 3.0, "face_fluxes": 185.0, "mom_fluxes": 420.0, "assemble": 100.0}
+JV_KERNELS = ["perturb", "eos", "face_fluxes", "mom_fluxes", "assemble"]
+# Algorithmic HBM bytes per cell of one launch of each Jv kernel (3D, FP64
+# state; reads and writes of the arrays each kernel must touch once).
+HBM_BYTES_PER_CELL = {"perturb": 5 * 8 * 4, "eos": 2 * 8 + 2 * 8, "face_fluxes": 5 * 8 + 2 * 8 + 6 * 8,
+                      "mom_fluxes": 3 * 8 + 3 * 8 + 9 * 8, "assemble": 5 * 8 + 8 + 6 * 8 + 9 * 8 + 3 * 5 * 8}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# FP64 FMA rate of this GPU model measured by a dependent-chain throughput
+# probe (8 independent DFMA chains per thread, 152x8 blocks of 256 threads):
+# 1.200 TFLOP/s (0.600 T DFMA/s); the nominal figure is 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.200
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(n):
+    import workloads as W
+    wl = W.config(4, n=(n, n, n))
+    # same physical time step at any resolution: CFL scales with n
+    wl.cfl_hydro = 200.0 * n / 256.0
+    return wl
+
+
+def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
+    import torch
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision)
+    S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
+    X0 = torch.as_tensor(wl.X0, dtype=torch.float64, device=device)
+    X = X0.clone()
+    dt = S.dt_from_cfl(X, wl.cfl_hydro)
+    for _ in range(warmup):
+        st = S.step(X, dt, NEWTON_TOL, ETA)
+    S.set_profiling(profile)
+    stats = []
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            stats.append(S.step(X, dt, NEWTON_TOL, ETA))
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S.set_profiling(False)
+    return S, X0, dt, ms, stats
+
+
+def e2e_arm(jf, wl, precision, steps, device, stream):
+    """Same metric through the public API with HOST buffers: every step copies
+    the state from pinned host memory to the device, steps, and copies the
+    new state back."""
+    import torch
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision)
+    S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
+    host = torch.as_tensor(wl.X0, dtype=torch.float64).pin_memory()
+    X = torch.empty_like(host, device=device)
+    with torch.cuda.stream(stream):
+        X.copy_(host, non_blocking=True)
+    dt = S.dt_from_cfl(X, wl.cfl_hydro)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            X.copy_(host, non_blocking=True)
+            S.step(X, dt, NEWTON_TOL, ETA)
+            host.copy_(X, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    nbytes = host.numel() * 8
+    return e0.elapsed_time(e1), nbytes
+
+
+def oracle_sample(n_small=32, steps=1):
+    """The CPU oracle as it stands: implicit steps of the same construction at
+    n_small^3 with the same physical dt; returns (s per step, threads)."""
+    import torch
+    from oracle import discretization as D
+    from oracle import jfnk as J
+    wl = make_workload(n_small)
+    P = D.Problem.from_workload(wl)
+    dt = D.cfl_dt(P, wl.X0, wl.cfl_hydro)
+    X = torch.as_tensor(wl.X0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        X, st = J.newton_step(P, X, dt, J.Options(precond=wl.precond, newton_tol=NEWTON_TOL, eta=ETA))
+    return (time.perf_counter() - t0) / steps, torch.get_num_threads()
+
+
+def reference_main(args, ws, rank):
+    n_small = 32
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(n_small, 1)
+    secs = []
+    threads = 1
+    for _ in range(args.steps):
+        s, threads = oracle_sample(n_small, 1)
+        secs.append(s)
+    mean = sum(secs) / len(secs)
+    scale = (n_small / args.n) ** 3
+    value = scale / mean
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"convbox3d {args.n}^3 (problem 4)", "global_batch": 1, "seq_len": 0,
+                       "parallelism": "replicas", "l2": "state larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"oracle implicit step at {n_small}^3 (same construction, same dt), "
+                                       f"time scaled by the cell ratio ({args.n}/{n_small})^3"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def kernel_main(args):
+    """--only jv|precond: repeated Jacobian-free products (or preconditioner
+    applies) at one state of the workload, for kernel profiling."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    import workloads as W
+    device = torch.device("cuda:0")
+    stream = torch.cuda.Stream(device)
+    wl = make_workload(args.n)
+    prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec)
+    S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
+    X = torch.as_tensor(wl.X0, dtype=torch.float64, device=device)
+    dt = S.dt_from_cfl(X, wl.cfl_hydro)
+    v = torch.as_tensor(W.random_vector(wl, 3), device=device).to(S.vdtype)
+    out = torch.empty_like(v)
+    call = (lambda: S.jv(X, dt, v, out)) if args.only == "jv" else (lambda: S.precond_apply(X, dt, v, out))
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            call()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"only": args.only, "n": args.n, "precision": args.precision, "ms_per_call": ms,
+                      "gcell_s": wl.ncell / (ms / 1e3) / 1e9}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per direction")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", choices=["jv", "precond"], default=None,
+                    help="time only repeated Jv or preconditioner calls (profiling)")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    args = ap.parse_args()
+    if args.only:
+        kernel_main(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        reference_main(args, ws, rank)
+        return
+
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device)
+    wl = make_workload(args.n)
+    peaks = load_peaks()
+
+    clocks = ClockSampler(local)
+    barrier(ws)
+    clocks.start()
+    S, X0, dt, ms_mixed, st_mixed = run_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream, True)
+    barrier(ws)
+    clk = clocks.stop()
+    ms_mixed = max_over_ranks(ws, ms_mixed)
+
+    fp64 = None
+    if not args.no_fp64:
+        S64, _, _, ms64, st64 = run_arm(jf, wl, jf.FP64, args.steps, args.warmup, device, stream, True)
+        ms64 = max_over_ranks(ws, ms64)
+        fp64 = {"steps_per_s": ws * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                "newton_per_step": sum(s["newton_iterations"] for s in st64) / len(st64),
+                "gmres_per_newton": sum(s["gmres_iterations_total"] for s in st64) /
+                max(1, sum(s["newton_iterations"] for s in st64)),
+                "jv_gcell_s": None}
+        jv64 = sum(s["jv_ms"] for s in st64)
+        njv64 = sum(s["jv_evaluations"] for s in st64)
+        if jv64 > 0:
+            fp64["jv_gcell_s"] = njv64 * wl.ncell / (jv64 / 1e3) / 1e9
+        del S64
+
+    steps_per_s = ws * args.steps / (ms_mixed / 1e3)
+    njv = sum(s["jv_evaluations"] for s in st_mixed)
+    jv_ms = sum(s["jv_ms"] for s in st_mixed)
+    kms = [sum(s["jv_kernel_ms"][q] for s in st_mixed) for q in range(5)]
+    launches = sum(s["kernel_launches"] for s in st_mixed)
+    dom = max(range(5), key=lambda q: kms[q])
+    name = JV_KERNELS[dom]
+    per_launch_ms = kms[dom] / max(1, njv)
+    flops = FP64_FLOPS_PER_CELL[name] * wl.ncell
+    achieved_tflops = flops / (per_launch_ms / 1e3) / 1e12
+    hbm_gbs = HBM_BYTES_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_src": "measured FP64 DFMA probe", "hbm_gbs": hbm_gbs,
+                "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"]}
+
+    e2e = None
+    if not args.no_e2e:
+        ms_e2e, nbytes = e2e_arm(jf, wl, jf.MIXED, args.steps, device, stream)
+        ms_e2e = max_over_ranks(ws, ms_e2e)
+        e2e = {"value": ws * args.steps / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_small = 32
+        s, threads = oracle_sample(n_small, 1)
+        v = (n_small / args.n) ** 3 / s
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"one oracle implicit step at {n_small}^3 (same construction and dt), "
+                         f"time scaled by the cell ratio ({args.n}/{n_small})^3"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64 residual / f32 Krylov",
+                "data": "synthetic",
+                "config": {"workload": f"convbox3d {args.n}^3 (problem 4), CFL_hydro {wl.cfl_hydro:g}, "
+                                       f"dt {dt:.4g}", "global_batch": 1, "seq_len": 0,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "state (670 MB/vector) larger than L2, no flush"},
+                "jv_gcell_s": njv * wl.ncell / (jv_ms / 1e3) / 1e9 if jv_ms > 0 else None,
+                "newton_per_step": sum(s["newton_iterations"] for s in st_mixed) / len(st_mixed),
+                "gmres_per_newton": sum(s["gmres_iterations_total"] for s in st_mixed) /
+                max(1, sum(s["newton_iterations"] for s in st_mixed)),
+                "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk,
+                "jv_kernel_ms_per_launch": {JV_KERNELS[q]: kms[q] / max(1, njv) for q in range(5)},
+                "precond_ms_per_apply": sum(s["precond_ms"] for s in st_mixed) /
+                max(1, sum(s["precond_applies"] for s in st_mixed)),
+                "ortho_ms_per_iteration": sum(s["ortho_ms"] for s in st_mixed) / max(1, njv)}
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

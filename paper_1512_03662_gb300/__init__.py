@@ -1,0 +1,255 @@
+"""Python binding of the JFNK CUDA library (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/jfnk.h with the
+same name; the numerical work runs in the library's CUDA kernels.  PyTorch
+supplies device memory (the workspace and the vectors) and the stream.  The
+library must have been built (`paper_1512_03662_gb300.build.build()`); there
+is no CPU fallback: a missing library raises at import of the first call.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libjfnk.so")
+
+JFNK_OK = 0
+JFNK_EINVAL = -1
+JFNK_ECUDA = -2
+JFNK_ENOMEM = -3
+JFNK_ENONFINITE = -4
+JFNK_ENOCONV_GMRES = 1
+JFNK_ENOCONV_NEWTON = 2
+
+BC_PERIODIC, BC_WALL = 0, 1
+ENERGY_INTERNAL, ENERGY_TOTAL = 0, 1
+PRECOND_NONE, PRECOND_SOUND, PRECOND_SOUND_DIFF = 0, 1, 2
+PERT_OLD, PERT_NEW = 0, 1
+FP64, MIXED = 0, 1
+MAX_NEWTON = 64
+
+
+class jfnk_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 3)]
+
+
+class jfnk_eos(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("energy_form", ctypes.c_int)]
+
+
+class jfnk_gravity(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double * 3)]
+
+
+class jfnk_conductivity(ctypes.Structure):
+    _fields_ = [("K0", ctypes.c_double), ("exponent", ctypes.c_double)]
+
+
+class jfnk_options(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("theta", "lambda_", "alpha1", "alpha2", "eta", "newton_tol")] + \
+               [(n, ctypes.c_int) for n in ("pert", "gmres_m", "gmres_max_it", "newton_min", "newton_max",
+                                             "precond", "mg_cycles", "mg_nu1", "mg_nu2", "precision", "reorth",
+                                             "fixed_iterations")]
+
+
+class jfnk_stats(ctypes.Structure):
+    _fields_ = [("newton_iterations", ctypes.c_int), ("gmres_iterations_total", ctypes.c_int),
+                ("gmres_iterations", ctypes.c_int * MAX_NEWTON), ("dx_inf", ctypes.c_double * MAX_NEWTON),
+                ("fhat_norm", ctypes.c_double * MAX_NEWTON), ("gmres_res", ctypes.c_double * MAX_NEWTON),
+                ("gmres_converged", ctypes.c_int * MAX_NEWTON), ("converged", ctypes.c_int),
+                ("jv_evaluations", ctypes.c_int), ("precond_applies", ctypes.c_int), ("jv_ms", ctypes.c_double),
+                ("precond_ms", ctypes.c_double), ("ortho_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
+                ("jv_kernel_ms", ctypes.c_double * 5), ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        k = self.newton_iterations
+        return {"newton_iterations": k, "gmres_iterations_total": self.gmres_iterations_total,
+                "gmres_iterations": list(self.gmres_iterations[:k]), "dx_inf": list(self.dx_inf[:k]),
+                "fhat_norm": list(self.fhat_norm[:k]), "gmres_res": list(self.gmres_res[:k]),
+                "gmres_converged": list(self.gmres_converged[:k]), "converged": bool(self.converged),
+                "jv_evaluations": self.jv_evaluations, "precond_applies": self.precond_applies,
+                "jv_ms": self.jv_ms, "precond_ms": self.precond_ms, "ortho_ms": self.ortho_ms,
+                "step_ms": self.step_ms, "jv_kernel_ms": list(self.jv_kernel_ms),
+                "kernel_launches": self.kernel_launches}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libjfnk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"JFNK CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_1512_03662_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, I, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+        DP = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "jfnk_default_options": (None, [ctypes.POINTER(jfnk_options)]),
+            "jfnk_create": (I, [ctypes.POINTER(jfnk_grid), ctypes.POINTER(jfnk_eos), ctypes.POINTER(jfnk_gravity),
+                                ctypes.POINTER(jfnk_conductivity), ctypes.POINTER(jfnk_options),
+                                ctypes.POINTER(P)]),
+            "jfnk_workspace_bytes": (S, [P]),
+            "jfnk_bind": (I, [P, P, S, P]),
+            "jfnk_vector_length": (ctypes.c_longlong, [P]),
+            "jfnk_set_options": (I, [P, ctypes.POINTER(jfnk_options)]),
+            "jfnk_residual": (I, [P, P, P, D, P]),
+            "jfnk_scaling": (I, [P, P, P, P, DP]),
+            "jfnk_jv": (I, [P, P, D, P, P, DP]),
+            "jfnk_precond_apply": (I, [P, P, D, P, P]),
+            "jfnk_linear_solve": (I, [P, P, P, D, P, ctypes.POINTER(jfnk_stats)]),
+            "jfnk_step": (I, [P, P, D, D, D, ctypes.POINTER(jfnk_stats)]),
+            "jfnk_dt_from_cfl": (I, [P, P, D, DP]),
+            "jfnk_set_profiling": (I, [P, I]),
+            "jfnk_last_error": (ctypes.c_char_p, [P]),
+            "jfnk_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["jfnk_default_options", "jfnk_create", "jfnk_workspace_bytes", "jfnk_bind", "jfnk_vector_length",
+            "jfnk_set_options", "jfnk_residual", "jfnk_scaling", "jfnk_jv", "jfnk_precond_apply",
+            "jfnk_linear_solve", "jfnk_step", "jfnk_dt_from_cfl", "jfnk_set_profiling", "jfnk_last_error",
+            "jfnk_destroy"]
+
+
+class JFNKError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def default_options(**kw) -> jfnk_options:
+    o = jfnk_options()
+    lib().jfnk_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, "lambda_" if k == "lam" else k, v)
+    return o
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One handle of the C library plus its torch-allocated workspace.
+
+    The methods mirror the C entry points (jfnk_residual -> residual, ...)
+    and take CUDA tensors laid out as described in include/jfnk.h."""
+
+    def __init__(self, ndim: int, n: Sequence[int], lo: Sequence[float], hi: Sequence[float],
+                 bc: Sequence[int], gamma: float, energy_form: int = 0, g: Sequence[float] = (0, 0, 0),
+                 K0: float = 0.0, chi_exp: float = 3.0, options: Optional[jfnk_options] = None,
+                 device: str = "cuda", stream: Optional[torch.cuda.Stream] = None):
+        L = lib()
+        gr = jfnk_grid(ndim, (ctypes.c_int * 3)(*n), (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi),
+                       (ctypes.c_int * 3)(*bc))
+        eo = jfnk_eos(gamma, energy_form)
+        gv = jfnk_gravity((ctypes.c_double * 3)(*g))
+        co = jfnk_conductivity(K0, chi_exp)
+        self.options = options if options is not None else default_options()
+        self.h = ctypes.c_void_p()
+        st = L.jfnk_create(ctypes.byref(gr), ctypes.byref(eo), ctypes.byref(gv), ctypes.byref(co),
+                           ctypes.byref(self.options), ctypes.byref(self.h))
+        if st != JFNK_OK:
+            msg = L.jfnk_last_error(self.h).decode() if self.h else "create failed"
+            if self.h:
+                L.jfnk_destroy(self.h)
+                self.h = None
+            raise JFNKError(st, msg)
+        self.device = torch.device(device)
+        self.nvec = int(L.jfnk_vector_length(self.h))
+        nbytes = int(L.jfnk_workspace_bytes(self.h))
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(L.jfnk_bind(self.h, ctypes.c_void_p(base + off), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.vdtype = torch.float32 if self.options.precision == MIXED else torch.float64
+
+    @staticmethod
+    def from_workload(wl, options: Optional[jfnk_options] = None, **kw) -> "Solver":
+        if options is None:
+            options = default_options(theta=wl.theta, precond=wl.precond)
+        return Solver(wl.ndim, wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.energy_form, wl.g, wl.K0, wl.chi_exp,
+                      options, **kw)
+
+    def _check(self, st: int, allow_positive: bool = False) -> int:
+        if st < 0 or (st > 0 and not allow_positive):
+            raise JFNKError(st, lib().jfnk_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jfnk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, dtype=torch.float64) -> torch.Tensor:
+        return torch.empty(self.nvec, dtype=dtype, device=self.device)
+
+    def set_options(self, options: jfnk_options):
+        self._check(lib().jfnk_set_options(self.h, ctypes.byref(options)))
+        self.options = options
+
+    def set_profiling(self, on: bool):
+        self._check(lib().jfnk_set_profiling(self.h, int(on)))
+
+    def residual(self, X: torch.Tensor, Xn: torch.Tensor, dt: float, out: Optional[torch.Tensor] = None):
+        F = self._vec() if out is None else out
+        self._check(lib().jfnk_residual(self.h, _ptr(X), _ptr(Xn), dt, _ptr(F)))
+        return F
+
+    def scaling(self, X: torch.Tensor):
+        L, R = self._vec(), self._vec()
+        xn = ctypes.c_double()
+        self._check(lib().jfnk_scaling(self.h, _ptr(X), _ptr(L), _ptr(R), ctypes.byref(xn)))
+        return L, R, xn.value
+
+    def jv(self, X: torch.Tensor, dt: float, v: torch.Tensor, out: Optional[torch.Tensor] = None):
+        Jv = self._vec(self.vdtype) if out is None else out
+        d = ctypes.c_double()
+        self._check(lib().jfnk_jv(self.h, _ptr(X), dt, _ptr(v), _ptr(Jv), ctypes.byref(d)))
+        return Jv, d.value
+
+    def precond_apply(self, X: torch.Tensor, dt: float, v: torch.Tensor, out: Optional[torch.Tensor] = None):
+        w = self._vec(self.vdtype) if out is None else out
+        self._check(lib().jfnk_precond_apply(self.h, _ptr(X), dt, _ptr(v), _ptr(w)))
+        return w
+
+    def linear_solve(self, X: torch.Tensor, Xn: torch.Tensor, dt: float):
+        dx = self._vec()
+        st = jfnk_stats()
+        code = self._check(lib().jfnk_linear_solve(self.h, _ptr(X), _ptr(Xn), dt, _ptr(dx), ctypes.byref(st)),
+                           allow_positive=True)
+        return dx, st.as_dict(), code
+
+    def step(self, X: torch.Tensor, dt: float, newton_tol: float = 0.0, krylov_tol: float = 0.0):
+        st = jfnk_stats()
+        code = self._check(lib().jfnk_step(self.h, _ptr(X), dt, newton_tol, krylov_tol, ctypes.byref(st)),
+                           allow_positive=True)
+        d = st.as_dict()
+        d["status"] = code
+        return d
+
+    def dt_from_cfl(self, X: torch.Tensor, cfl: float) -> float:
+        dt = ctypes.c_double()
+        self._check(lib().jfnk_dt_from_cfl(self.h, _ptr(X), cfl, ctypes.byref(dt)))
+        return dt.value

@@ -1,0 +1,128 @@
+// Shared device-side definitions of the JFNK library: grid descriptor,
+// neighbour indexing with periodic / reflecting-wall ghosts, the van Leer
+// slope, and deterministic block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jfnk {
+
+constexpr int kBlock = 256;          // threads per block of the pointwise kernels
+constexpr int kRedBlocks = 1024;     // fixed block count of grid-stride reductions
+
+struct Grid {
+    int ndim;
+    int n[3];
+    long long ncell;
+    double dx[3], idx[3], idx2[3];
+    int bc[3];                       // 0 periodic, 1 wall
+    double gamma, gm1;
+    double g[3];
+    double K0, chi_exp;
+    int energy_form;                 // 0 internal e, 1 total eps_t
+    double theta;
+};
+
+struct Idx3 { int i[3]; };
+
+__device__ __forceinline__ Idx3 decompose(const Grid& G, long long c) {
+    Idx3 r;
+    r.i[0] = (int)(c % G.n[0]);
+    long long t = c / G.n[0];
+    r.i[1] = (int)(t % G.n[1]);
+    r.i[2] = (int)(t / G.n[1]);
+    return r;
+}
+
+__device__ __forceinline__ long long flat(const Grid& G, int i0, int i1, int i2) {
+    return ((long long)i2 * G.n[1] + i1) * G.n[0] + i0;
+}
+
+// Cell-quantity index of position k along a direction of size n: periodic
+// wrap, or mirror about the wall faces (k -> -k-1, k -> 2n-1-k).
+__device__ __forceinline__ int cell_map(int k, int n, int bc) {
+    if (bc == 0) {
+        k %= n;
+        return k < 0 ? k + n : k;
+    }
+    if (k < 0) return -k - 1;
+    if (k >= n) return 2 * n - 1 - k;
+    return k;
+}
+
+// Load of a cell quantity at (pos + off) with ghost mapping in every direction.
+__device__ __forceinline__ double load_cell(const Grid& G, const double* __restrict__ f, const Idx3& p,
+                                            int o0, int o1, int o2) {
+    int a = cell_map(p.i[0] + o0, G.n[0], G.bc[0]);
+    int b = cell_map(p.i[1] + o1, G.n[1], G.bc[1]);
+    int c = cell_map(p.i[2] + o2, G.n[2], G.bc[2]);
+    return __ldg(f + flat(G, a, b, c));
+}
+
+// Load of the velocity normal to the faces of direction `c` at slot
+// (pos + off): odd mirror about the wall faces, zero on both wall faces;
+// cell mapping in the other directions.
+__device__ __forceinline__ double load_normal(const Grid& G, const double* __restrict__ u, int c, const Idx3& p,
+                                              int o0, int o1, int o2) {
+    int k[3] = {p.i[0] + o0, p.i[1] + o1, p.i[2] + o2};
+    double sgn = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (d == c && G.bc[d] == 1) {
+            int n = G.n[d];
+            int kk = k[d];
+            if (kk == 0 || kk == n) return 0.0;
+            if (kk < 0) { kk = -kk; sgn = -sgn; }
+            else if (kk > n) { kk = 2 * n - kk; sgn = -sgn; }
+            k[d] = kk;
+        } else {
+            k[d] = cell_map(k[d], G.n[d], G.bc[d]);
+        }
+    }
+    return sgn * __ldg(u + flat(G, k[0], k[1], k[2]));
+}
+
+// True when slot p is the wall face of direction c.
+__device__ __forceinline__ bool is_wall_slot(const Grid& G, int c, const Idx3& p) {
+    return G.bc[c] == 1 && p.i[c] == 0;
+}
+
+// van Leer (1974) harmonic slope: 2ab/(a+b) if ab > 0 else 0.
+__device__ __forceinline__ double vanleer(double a, double b) {
+    double ab = a * b;
+    return ab > 0.0 ? (2.0 * ab) / (a + b) : 0.0;
+}
+
+template <typename T> struct Acc { typedef double type; };
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+template <int BS>
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) {
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+}  // namespace jfnk

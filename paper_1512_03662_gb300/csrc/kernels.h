@@ -1,0 +1,113 @@
+// Host-side launch interface between the solver engine and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace jfnk {
+
+// number of kernels launched through the launchers below (profiling aid)
+extern long long g_launch_count;
+
+enum { kModeG = 0, kModeBn = 1, kModeRes = 2, kModeNewton = 3, kModeJv = 4 };
+
+// device scalar slots (double array `scal` in the workspace)
+enum {
+    kSlotXhatNorm = 0,   // ||R^-1 X||_2
+    kSlotDelta = 1,      // perturbation delta of the current Jv
+    kSlotBeta = 2,       // ||b||_2 of the current GMRES cycle
+    kSlotRes = 3,        // GMRES residual estimate |g_{j+1}|
+    kSlotDxInf = 4,      // ||dxhat||_inf
+    kSlotZnorm = 5,      // ||z||_2 of the last preconditioned vector
+    kSlotMaxSpeed = 6,   // max |u| + c_s
+    kSlotTmp = 7,
+    kSlotBeta0 = 8,
+    kNumSlots = 16
+};
+
+// residual.cu
+void launch_eos(const Grid& G, const double* X, double* p, double* T, cudaStream_t s);
+template <typename TZ>
+void launch_perturb(const Grid& G, const double* X, const TZ* z, const double* R, const double* scal, int slot,
+                    double* Xp, cudaStream_t s);
+void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
+                        cudaStream_t s);
+void launch_mom_fluxes(const Grid& G, const double* X, const double* Fm, double* Psi, cudaStream_t s);
+void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
+                   double* Psi, cudaStream_t s);
+template <int MODE, typename TO>
+void launch_assemble(const Grid& G, const double* X, const double* p, const double* Fm, const double* FE,
+                     const double* Psi, const double* bn, const double* G0, const double* Linv, const double* scal,
+                     int slot, double dt, double* outd, TO* outb, cudaStream_t s);
+void launch_scaling(const Grid& G, const double* X, double a1, double a2, double* L, double* R, double* Linv,
+                    double* Rinv, double* partials, cudaStream_t s);
+void launch_signal_speed(const Grid& G, const double* X, double* partials, cudaStream_t s);
+unsigned cell_blocks(const Grid& G);
+
+// krylov.cu
+// finalize: scal[slot] = op(partials[0..n)) with op 0 = sqrt(sum), 1 = sum, 2 = max
+void launch_finalize(const double* partials, int n, double* scal, int slot, int op, cudaStream_t s);
+// delta = lambda (lambda + xhat / ||z||) (pert 0) or the pert_new rule (pert 1,
+// uses scal[kSlotTmp] = xhat . z and scal[kSlotZnorm])
+void launch_delta(double* scal, double lambda, int pert, cudaStream_t s);
+template <typename T>
+void launch_norm2_partials(const T* x, long long n, double* partials, cudaStream_t s);
+template <typename T>
+void launch_dot_partials(const double* a, const double* ainv_scale, const T* b, long long n, double* partials,
+                         cudaStream_t s);
+template <typename T>
+void launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s);
+void launch_multidot_finalize(const double* partials, int nblocks, int nv, const double* vscale, double* hcol,
+                              int accumulate, cudaStream_t s);
+template <typename T>
+void launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
+                      double* partials, cudaStream_t s);
+// hcol[j+1] = norm, vscale[j+1] = 1/norm
+void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s);
+void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* scal, cudaStream_t s);
+void launch_backsolve(const double* H, int ldh, int k, const double* g, double* y, cudaStream_t s);
+template <typename T>
+void launch_update(double* x, const T* Z, long long ld, int k, const double* y, long long n, cudaStream_t s);
+template <typename TS, typename TD>
+void launch_scale_copy(const TS* src, double alpha, const double* scal, int slot, int invert, TD* dst, long long n,
+                       cudaStream_t s);
+void launch_newton_update(double* X, const double* R, const double* dxh, long long n, double* partials,
+                          cudaStream_t s);
+template <typename T>
+void launch_zero(T* x, long long n, cudaStream_t s);
+template <typename T>
+void launch_restart_residual(T* r, const double* G0, const double* bn, const double* Linv, long long n,
+                             cudaStream_t s);
+void launch_init_cycle(double* scal, double* g, double* vscale, int m, cudaStream_t s);
+void launch_add_col(double* col, const double* other, int n, cudaStream_t s);
+
+// precond.cu
+struct MGLevel {
+    int n[3];
+    long long ncell;
+    double h[3], ih2[3];
+    void* M;     // nf*nf fields
+    void* K;     // nf*ndim fields (coefficient on the lower face)
+    void* x;     // nf fields
+    void* rhs;   // nf fields
+};
+
+template <typename T>
+void launch_si_setup(const Grid& G, const double* X, double dt, int nf, MGLevel& L0, cudaStream_t s);
+template <typename T>
+void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStream_t s);
+template <typename TV, typename T>
+void launch_precond_in(const Grid& G, const double* X, const double* L, const TV* v, const double* vscale, int vslot,
+                       double dt, int nf, T* rp, T* re, T* ru, MGLevel& L0, cudaStream_t s);
+template <typename T>
+void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s);
+template <typename T>
+void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
+template <typename T>
+void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
+template <typename T>
+void launch_coarsest(int nf, MGLevel& C, cudaStream_t s);
+template <typename T, typename TO>
+void launch_precond_out(const Grid& G, const double* X, const double* Rinv, double dt, int nf, const T* rp,
+                        const T* re, const T* ru, const MGLevel& L0, TO* z, double* partials, cudaStream_t s);
+
+}  // namespace jfnk

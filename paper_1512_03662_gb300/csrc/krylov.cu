@@ -1,0 +1,407 @@
+// GMRES kernels (paper Sect. 4.1, Eq. forcing_term; restarted GMRES of Saad &
+// Schultz 1986 with classical Gram-Schmidt):
+//   * multi-dot: h_i = <v_i, w> for all basis vectors in ONE pass over w,
+//     accumulated in double whatever the storage type;
+//   * AXPY + norm: w -= sum_i h_i s_i v_i and ||w||^2 in the same pass;
+//   * lazy normalisation: v_{j+1} keeps the unnormalised w, its scale
+//     s_{j+1} = 1/||w|| is applied by every reader, which saves a pass;
+//   * Givens rotations and the triangular solve run on the device in one
+//     thread (m <= 64), so the host only reads the residual estimate.
+// Reductions are two-stage with a fixed block count and a fixed summation
+// order, so results are bit-reproducible from run to run.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace jfnk {
+
+__global__ void k_finalize(const double* __restrict__ partials, int n, double* scal, int slot, int op) {
+    __shared__ double sh[32];
+    double v = (op == 2) ? 0.0 : 0.0;
+    bool nan = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double x = partials[i];
+        if (!(x == x)) nan = true;
+        if (op == 2) v = fmax(v, x); else v += x;
+    }
+    double r = (op == 2) ? block_max<1024>(v, sh) : block_sum<1024>(v, sh);
+    int anynan = __syncthreads_or(nan);
+    if (threadIdx.x == 0) {
+        if (anynan) r = __longlong_as_double(0x7ff8000000000000ULL);
+        scal[slot] = (op == 0) ? sqrt(r) : r;
+    }
+}
+
+void launch_finalize(const double* partials, int n, double* scal, int slot, int op, cudaStream_t s) {
+    ++g_launch_count;
+    k_finalize<<<1, 1024, 0, s>>>(partials, n, scal, slot, op);
+}
+
+__global__ void k_delta(double* scal, double lambda, int pert) {
+    double zn = scal[kSlotZnorm];
+    if (pert == 0) {
+        scal[kSlotDelta] = lambda * (lambda + scal[kSlotXhatNorm] / zn);
+    } else {
+        double uv = scal[kSlotTmp];
+        double sgn = uv >= 0.0 ? 1.0 : -1.0;
+        scal[kSlotDelta] = lambda * (1e-12 / lambda + fabs(uv) / (zn * zn)) * sgn;
+    }
+}
+
+void launch_delta(double* scal, double lambda, int pert, cudaStream_t s) { k_delta<<<1, 1, 0, s>>>(scal, lambda, pert); }
+
+template <typename T>
+__global__ void k_norm2(const T* __restrict__ x, long long n, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = (double)x[i];
+        acc += v * v;
+    }
+    double s = block_sum<kBlock>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+void launch_norm2_partials(const T* x, long long n, double* partials, cudaStream_t s) {
+    ++g_launch_count;
+    k_norm2<T><<<kRedBlocks, kBlock, 0, s>>>(x, n, partials);
+}
+template void launch_norm2_partials<double>(const double*, long long, double*, cudaStream_t);
+template void launch_norm2_partials<float>(const float*, long long, double*, cudaStream_t);
+
+// partial sums of (a_i * ainv_i) * b_i  (used for x^ . z with x^ = X R^-1)
+template <typename T>
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ ainv, const T* __restrict__ b,
+                      long long n, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (a[i] * ainv[i]) * (double)b[i];
+    double s = block_sum<kBlock>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+void launch_dot_partials(const double* a, const double* ainv, const T* b, long long n, double* partials,
+                         cudaStream_t s) {
+    ++g_launch_count;
+    k_dot<T><<<kRedBlocks, kBlock, 0, s>>>(a, ainv, b, n, partials);
+}
+template void launch_dot_partials<double>(const double*, const double*, const double*, long long, double*, cudaStream_t);
+template void launch_dot_partials<float>(const double*, const double*, const float*, long long, double*, cudaStream_t);
+
+// one pass over w: partials[blk * NV + i] = sum over the block's elements of v_i * w
+template <typename T, int NV>
+__global__ void k_multidot(const T* __restrict__ V, long long ld, const T* __restrict__ w, long long n,
+                           double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double wk = (double)w[k];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += (double)V[i * ld + k] * wk;
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = block_sum<kBlock>(acc[i], sh);
+        if (threadIdx.x == 0) partials[blockIdx.x * NV + i] = s;
+    }
+}
+
+// generic fallback for any count: loops over groups of 8
+template <typename T>
+__global__ void k_multidot_group(const T* __restrict__ V, long long ld, int i0, int ni, int nvtot,
+                                 const T* __restrict__ w, long long n, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double wk = (double)w[k];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < ni) acc[i] += (double)V[(i0 + i) * ld + k] * wk;
+    }
+    for (int i = 0; i < ni; ++i) {
+        double s = block_sum<kBlock>(acc[i], sh);
+        if (threadIdx.x == 0) partials[blockIdx.x * nvtot + i0 + i] = s;
+    }
+}
+
+template <typename T>
+void launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s) {
+    switch (nv) {
+#define CASE(N) case N: ++g_launch_count; k_multidot<T, N><<<kRedBlocks, kBlock, 0, s>>>(V, ld, w, n, partials); return;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+        CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
+#undef CASE
+        default:
+            for (int i0 = 0; i0 < nv; i0 += 8) {
+                int ni = nv - i0 < 8 ? nv - i0 : 8;
+                ++g_launch_count;
+                k_multidot_group<T><<<kRedBlocks, kBlock, 0, s>>>(V, ld, i0, ni, nv, w, n, partials);
+            }
+    }
+}
+template void launch_multidot<double>(const double*, long long, int, const double*, long long, double*, cudaStream_t);
+template void launch_multidot<float>(const float*, long long, int, const float*, long long, double*, cudaStream_t);
+
+// hcol[i] (+)= vscale[i] * sum_b partials[b * nv + i]; one block per i
+__global__ void k_multidot_finalize(const double* __restrict__ partials, int nblocks, int nv,
+                                    const double* __restrict__ vscale, double* hcol, int accumulate) {
+    __shared__ double sh[32];
+    int i = blockIdx.x;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[b * nv + i];
+    double r = block_sum<kBlock>(v, sh);
+    if (threadIdx.x == 0) {
+        double h = r * vscale[i];
+        hcol[i] = accumulate ? hcol[i] + h : h;
+    }
+}
+
+void launch_multidot_finalize(const double* partials, int nblocks, int nv, const double* vscale, double* hcol,
+                              int accumulate, cudaStream_t s) {
+    ++g_launch_count;
+    k_multidot_finalize<<<nv, kBlock, 0, s>>>(partials, nblocks, nv, vscale, hcol, accumulate);
+}
+
+// w -= sum_i (h_i s_i) v_i ; partial ||w||^2
+template <typename T, int NV>
+__global__ void k_axpy_norm(T* __restrict__ w, const T* __restrict__ V, long long ld, const double* __restrict__ hcol,
+                            const double* __restrict__ vscale, long long n, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    __shared__ double coef[64];
+    if (threadIdx.x < NV) coef[threadIdx.x] = hcol[threadIdx.x] * vscale[threadIdx.x];
+    __syncthreads();
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double x = (double)w[k];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) x -= coef[i] * (double)V[i * ld + k];
+        T xs = (T)x;
+        w[k] = xs;
+        double xd = (double)xs;
+        acc += xd * xd;
+    }
+    double s = block_sum<kBlock>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_axpy_norm_dyn(T* __restrict__ w, const T* __restrict__ V, long long ld, int nv,
+                                const double* __restrict__ hcol, const double* __restrict__ vscale, long long n,
+                                double* __restrict__ partials) {
+    __shared__ double sh[32];
+    __shared__ double coef[64];
+    if (threadIdx.x < nv) coef[threadIdx.x] = hcol[threadIdx.x] * vscale[threadIdx.x];
+    __syncthreads();
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double x = (double)w[k];
+        for (int i = 0; i < nv; ++i) x -= coef[i] * (double)V[i * ld + k];
+        T xs = (T)x;
+        w[k] = xs;
+        double xd = (double)xs;
+        acc += xd * xd;
+    }
+    double s = block_sum<kBlock>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+void launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
+                      double* partials, cudaStream_t s) {
+    switch (nv) {
+#define CASE(N) case N: ++g_launch_count; k_axpy_norm<T, N><<<kRedBlocks, kBlock, 0, s>>>(w, V, ld, hcol, vscale, n, partials); return;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+        CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
+#undef CASE
+        default:
+            ++g_launch_count;
+            k_axpy_norm_dyn<T><<<kRedBlocks, kBlock, 0, s>>>(w, V, ld, nv, hcol, vscale, n, partials);
+    }
+}
+template void launch_axpy_norm<double>(double*, const double*, long long, int, const double*, const double*, long long,
+                                       double*, cudaStream_t);
+template void launch_axpy_norm<float>(float*, const float*, long long, int, const double*, const double*, long long,
+                                      double*, cudaStream_t);
+
+__global__ void k_set_subdiag(double* scal, double* hcol, int j, double* vscale) {
+    double nrm = scal[kSlotTmp];
+    hcol[j + 1] = nrm;
+    vscale[j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+}
+
+void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s) {
+    ++g_launch_count;
+    k_set_subdiag<<<1, 1, 0, s>>>(scal, hcol, j, vscale);
+}
+
+// Column j of the Hessenberg matrix H (column-major, leading dim ldh): apply
+// the previous rotations, form rotation j, update g; scal[kSlotRes] = |g_{j+1}|.
+__global__ void k_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* scal) {
+    double* h = H + (long long)j * ldh;
+    for (int i = 0; i < j; ++i) {
+        double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    double a = h[j], b = h[j + 1];
+    double den = sqrt(a * a + b * b);
+    double c = 1.0, s = 0.0;
+    if (den != 0.0) { c = a / den; s = b / den; }
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = c * a + s * b;
+    h[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    scal[kSlotRes] = fabs(g[j + 1]);
+}
+
+void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* scal, cudaStream_t s) {
+    ++g_launch_count;
+    k_givens<<<1, 1, 0, s>>>(H, ldh, j, cs, sn, g, scal);
+}
+
+__global__ void k_backsolve(const double* H, int ldh, int k, const double* g, double* y) {
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int l = i + 1; l < k; ++l) s -= H[(long long)l * ldh + i] * y[l];
+        y[i] = s / H[(long long)i * ldh + i];
+    }
+}
+
+void launch_backsolve(const double* H, int ldh, int k, const double* g, double* y, cudaStream_t s) {
+    ++g_launch_count;
+    k_backsolve<<<1, 1, 0, s>>>(H, ldh, k, g, y);
+}
+
+// x += sum_{i<k} y_i Z_i
+template <typename T>
+__global__ void k_update(double* __restrict__ x, const T* __restrict__ Z, long long ld, int k,
+                         const double* __restrict__ y, long long n) {
+    __shared__ double ys[64];
+    if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double v = x[e];
+        for (int i = 0; i < k; ++i) v = v + ys[i] * (double)Z[i * ld + e];
+        x[e] = v;
+    }
+}
+
+template <typename T>
+void launch_update(double* x, const T* Z, long long ld, int k, const double* y, long long n, cudaStream_t s) {
+    ++g_launch_count;
+    k_update<T><<<kRedBlocks, kBlock, 0, s>>>(x, Z, ld, k, y, n);
+}
+template void launch_update<double>(double*, const double*, long long, int, const double*, long long, cudaStream_t);
+template void launch_update<float>(double*, const float*, long long, int, const double*, long long, cudaStream_t);
+
+// dst = src * (alpha, or scal[slot], or 1/scal[slot])
+template <typename TS, typename TD>
+__global__ void k_scale_copy(const TS* __restrict__ src, double alpha, const double* scal, int slot, int invert,
+                             TD* __restrict__ dst, long long n) {
+    double a = alpha;
+    if (slot >= 0) a = invert ? 1.0 / scal[slot] : scal[slot];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = (TD)((double)src[e] * a);
+}
+
+template <typename TS, typename TD>
+void launch_scale_copy(const TS* src, double alpha, const double* scal, int slot, int invert, TD* dst, long long n,
+                       cudaStream_t s) {
+    ++g_launch_count;
+    k_scale_copy<TS, TD><<<kRedBlocks, kBlock, 0, s>>>(src, alpha, scal, slot, invert, dst, n);
+}
+template void launch_scale_copy<double, double>(const double*, double, const double*, int, int, double*, long long, cudaStream_t);
+template void launch_scale_copy<double, float>(const double*, double, const double*, int, int, float*, long long, cudaStream_t);
+template void launch_scale_copy<float, float>(const float*, double, const double*, int, int, float*, long long, cudaStream_t);
+template void launch_scale_copy<float, double>(const float*, double, const double*, int, int, double*, long long, cudaStream_t);
+
+// X += R dxh ; partial max |dxh| (NaN propagates)
+__global__ void k_newton_update(double* __restrict__ X, const double* __restrict__ R, const double* __restrict__ dxh,
+                                long long n, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double m = 0.0;
+    bool nan = false;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double d = dxh[e];
+        X[e] = X[e] + R[e] * d;
+        double a = fabs(d);
+        if (!(a == a)) nan = true;
+        m = fmax(m, a);
+    }
+    double r = block_max<kBlock>(m, sh);
+    int anynan = __syncthreads_or(nan);
+    if (threadIdx.x == 0) partials[blockIdx.x] = anynan ? __longlong_as_double(0x7ff8000000000000ULL) : r;
+}
+
+void launch_newton_update(double* X, const double* R, const double* dxh, long long n, double* partials,
+                          cudaStream_t s) {
+    ++g_launch_count;
+    k_newton_update<<<kRedBlocks, kBlock, 0, s>>>(X, R, dxh, n, partials);
+}
+
+template <typename T>
+__global__ void k_zero(T* x, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        x[e] = (T)0;
+}
+
+template <typename T>
+void launch_zero(T* x, long long n, cudaStream_t s) { k_zero<T><<<kRedBlocks, kBlock, 0, s>>>(x, n); }
+template void launch_zero<double>(double*, long long, cudaStream_t);
+template void launch_zero<float>(float*, long long, cudaStream_t);
+
+// r = b - r with b = -(G0 - b^n) L^-1 (the Newton right-hand side, rebuilt in
+// double for a GMRES restart); r holds J^ x on entry
+template <typename T>
+__global__ void k_restart_residual(T* r, const double* __restrict__ G0, const double* __restrict__ bn,
+                                   const double* __restrict__ Linv, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double b = -((G0[e] - bn[e]) * Linv[e]);
+        r[e] = (T)(b - (double)r[e]);
+    }
+}
+
+template <typename T>
+void launch_restart_residual(T* r, const double* G0, const double* bn, const double* Linv, long long n,
+                             cudaStream_t s) {
+    ++g_launch_count;
+    k_restart_residual<T><<<kRedBlocks, kBlock, 0, s>>>(r, G0, bn, Linv, n);
+}
+template void launch_restart_residual<double>(double*, const double*, const double*, const double*, long long,
+                                              cudaStream_t);
+template void launch_restart_residual<float>(float*, const double*, const double*, const double*, long long,
+                                             cudaStream_t);
+
+// start of a GMRES cycle: g = (beta, 0, ...), vscale[0] = 1/beta
+__global__ void k_init_cycle(double* scal, double* g, double* vscale, int m) {
+    double beta = scal[kSlotBeta];
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    vscale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+void launch_init_cycle(double* scal, double* g, double* vscale, int m, cudaStream_t s) {
+    ++g_launch_count;
+    k_init_cycle<<<1, 1, 0, s>>>(scal, g, vscale, m);
+}
+
+// column += other (second Gram-Schmidt pass)
+__global__ void k_add_col(double* col, const double* other, int n) {
+    int i = threadIdx.x;
+    if (i < n) col[i] += other[i];
+}
+
+void launch_add_col(double* col, const double* other, int n, cudaStream_t s) {
+    ++g_launch_count;
+    k_add_col<<<1, 64, 0, s>>>(col, other, n);
+}
+
+}  // namespace jfnk

@@ -1,0 +1,609 @@
+// Physics-based preconditioner (paper Sects. 3.2-3.4 and 4.3).
+//
+//   w = R^-1 dX/dV J~_V^-1 dV/dU L v
+//
+// k_precond_in   v -> r_V = dV/dU L v, factored as dV/dX dX/dU (App. B); the
+//                velocity rows act face by face, r_u = (r_rhou - u rbar_rho)/rho_f;
+//                the multigrid right-hand side is B^-1 (r_p, r_e), B the 2x2
+//                matrix of the Laplacian coefficients of the p and e rows
+//                (1x1, B = theta^2 dt Gamma1 p, for the sound-only scheme).
+// k_si_setup     cell matrix M = B^-1/dt and face coefficients K_p = 1/rho_f,
+//                K_e = chi_f/c_v of the equivalent system
+//                    M x - [div(K_p grad dp); div(K_e grad de)] = B^-1 r,
+//                from the current Newton iterate.
+// multigrid      fixed V-cycles: red-black (point-block) Gauss-Seidel,
+//                mean restriction, cell-centred linear prolongation, exact
+//                one-cell coarsest level; coarse coefficients by averaging.
+// k_precond_out  de from the identity of Sect. 3.3.4 (sound scheme) or from
+//                the coupled solve; du_f = dt (r_u - theta rho_f^-1 grad dp);
+//                dX = dX/dV dV; z = R^-1 dX and partial sums of |z|^2.
+// The multigrid runs in the basis precision T (float in mixed mode); the
+// pointwise transforms compute in double and store T.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace jfnk {
+
+static inline unsigned nb(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+struct LvlDev {
+    int n[3];
+    long long nc;
+    double ih2[3];
+};
+
+static inline LvlDev lvl(const MGLevel& L) {
+    LvlDev d;
+    for (int i = 0; i < 3; ++i) { d.n[i] = L.n[i]; d.ih2[i] = L.ih2[i]; }
+    d.nc = L.ncell;
+    return d;
+}
+
+__device__ __forceinline__ long long lflat(const LvlDev& L, int a, int b, int c) {
+    return ((long long)c * L.n[1] + b) * L.n[0] + a;
+}
+
+__device__ __forceinline__ int wrapi(int k, int n) { return k < 0 ? k + n : (k >= n ? k - n : k); }
+
+__device__ __forceinline__ double conductivity_si(const Grid& G, double T) {
+    return G.chi_exp == 3.0 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+}
+
+// ---------------------------------------------------------------------------
+// coefficients at the current iterate
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double e_internal_at(const Grid& G, const double* X, const Idx3& P, int o0, int o1, int o2) {
+    const long long nc = G.ncell;
+    double E = load_cell(G, X + nc, P, o0, o1, o2);
+    if (G.energy_form == 0) return E;
+    Idx3 Q;
+    Q.i[0] = cell_map(P.i[0] + o0, G.n[0], G.bc[0]);
+    Q.i[1] = cell_map(P.i[1] + o1, G.n[1], G.bc[1]);
+    Q.i[2] = cell_map(P.i[2] + o2, G.n[2], G.bc[2]);
+    double ke = 0.0;
+    for (int d = 0; d < G.ndim; ++d) {
+        const double* u = X + (2 + d) * nc;
+        int o[3] = {0, 0, 0};
+        o[d] = 1;
+        double ul = load_normal(G, u, d, Q, 0, 0, 0);
+        double uu = load_normal(G, u, d, Q, o[0], o[1], o[2]);
+        ke = ke + 0.25 * (ul * ul + uu * uu);
+    }
+    return E - ke;
+}
+
+struct Binv2 { double b00, b01, b10, b11, bpp; };
+
+__device__ __forceinline__ Binv2 si_B(const Grid& G, double rho, double p, double dt, int nf) {
+    const double th = G.theta;
+    Binv2 B;
+    B.bpp = th * th * dt * G.gamma * p;
+    if (nf == 2) {
+        double bpe = th * (G.gamma - 1.0);
+        double bep = th * th * dt * p / rho;
+        double bee = th / rho;
+        double det = B.bpp * bee - bpe * bep;
+        B.b00 = bee / det;
+        B.b01 = -bpe / det;
+        B.b10 = -bep / det;
+        B.b11 = B.bpp / det;
+    } else {
+        B.b00 = B.b01 = B.b10 = B.b11 = 0.0;
+    }
+    return B;
+}
+
+template <typename T>
+__global__ void k_si_setup(Grid G, const double* __restrict__ X, double dt, int nf, T* __restrict__ M,
+                           T* __restrict__ K) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= G.ncell) return;
+    const long long nc = G.ncell;
+    Idx3 P = decompose(G, cc);
+    double rho = X[cc];
+    double e = e_internal_at(G, X, P, 0, 0, 0);
+    double p = G.gm1 * rho * e;
+    Binv2 B = si_B(G, rho, p, dt, nf);
+    if (nf == 1) {
+        M[cc] = (T)((1.0 / dt) / B.bpp);
+    } else {
+        M[0 * nc + cc] = (T)(B.b00 / dt);
+        M[1 * nc + cc] = (T)(B.b01 / dt);
+        M[2 * nc + cc] = (T)(B.b10 / dt);
+        M[3 * nc + cc] = (T)(B.b11 / dt);
+    }
+    const double cv = 1.0 / G.gm1;
+    const double chi0 = (G.K0 != 0.0) ? conductivity_si(G, G.gm1 * e) : 0.0;
+    for (int c = 0; c < G.ndim; ++c) {
+        double m = (is_wall_slot(G, c, P) || G.n[c] == 1) ? 0.0 : 1.0;
+        int o[3] = {0, 0, 0};
+        o[c] = -1;
+        double rl = load_cell(G, X, P, o[0], o[1], o[2]);
+        double rho_f = 0.5 * (rl + rho);
+        K[(0 * G.ndim + c) * nc + cc] = (T)(m / rho_f);
+        if (nf == 2) {
+            double chil = 0.0;
+            if (G.K0 != 0.0) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
+            K[(1 * G.ndim + c) * nc + cc] = (T)(m * (0.5 * (chil + chi0)) / cv);
+        }
+    }
+}
+
+template <typename T>
+void launch_si_setup(const Grid& G, const double* X, double dt, int nf, MGLevel& L0, cudaStream_t s) {
+    ++g_launch_count;
+    k_si_setup<T><<<nb(G.ncell), kBlock, 0, s>>>(G, X, dt, nf, (T*)L0.M, (T*)L0.K);
+}
+template void launch_si_setup<double>(const Grid&, const double*, double, int, MGLevel&, cudaStream_t);
+template void launch_si_setup<float>(const Grid&, const double*, double, int, MGLevel&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// coarse coefficients
+// ---------------------------------------------------------------------------
+
+// mean over the children of coarse cell (a,b,c), pairs along x, then y, then z
+template <typename T>
+__device__ __forceinline__ double child_mean(const T* f, const LvlDev& F, const int cd[3], int a, int b, int c) {
+    int nx = cd[0] ? 2 : 1, ny = cd[1] ? 2 : 1, nz = cd[2] ? 2 : 1;
+    int x0 = cd[0] ? 2 * a : a, y0 = cd[1] ? 2 * b : b, z0 = cd[2] ? 2 * c : c;
+    double zs[2];
+    for (int kz = 0; kz < nz; ++kz) {
+        double ys[2];
+        for (int ky = 0; ky < ny; ++ky) {
+            long long base = lflat(F, x0, y0 + ky, z0 + kz);
+            double v0 = (double)f[base];
+            ys[ky] = (nx == 2) ? (v0 + (double)f[base + 1]) / 2.0 : v0;
+        }
+        zs[kz] = (ny == 2) ? (ys[0] + ys[1]) / 2.0 : ys[0];
+    }
+    return (nz == 2) ? (zs[0] + zs[1]) / 2.0 : zs[0];
+}
+
+template <typename T>
+__global__ void k_coarsen(int nf, int ndim, LvlDev F, LvlDev C, const T* __restrict__ Mf, const T* __restrict__ Kf,
+                          T* __restrict__ Mc, T* __restrict__ Kc) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= C.nc) return;
+    int a = (int)(cc % C.n[0]);
+    long long t = cc / C.n[0];
+    int b = (int)(t % C.n[1]);
+    int c = (int)(t / C.n[1]);
+    int cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
+    for (int q = 0; q < nf * nf; ++q) Mc[q * C.nc + cc] = (T)child_mean(Mf + q * F.nc, F, cd, a, b, c);
+    for (int f = 0; f < nf; ++f) {
+        for (int d = 0; d < ndim; ++d) {
+            const T* k = Kf + (f * ndim + d) * F.nc;
+            double v = 0.0;
+            if (C.n[d] > 1) {
+                // fine lower faces of the even children along d, mean over the other coarsened dims
+                int cd2[3] = {cd[0], cd[1], cd[2]};
+                cd2[d] = 0;
+                int pos[3] = {a, b, c};
+                int fx = cd[0] ? 2 * a : a, fy = cd[1] ? 2 * b : b, fz = cd[2] ? 2 * c : c;
+                (void)pos;
+                int nx = cd2[0] ? 2 : 1, ny = cd2[1] ? 2 : 1, nz = cd2[2] ? 2 : 1;
+                double zs[2];
+                for (int kz = 0; kz < nz; ++kz) {
+                    double ys[2];
+                    for (int ky = 0; ky < ny; ++ky) {
+                        long long base = lflat(F, fx, fy + ky, fz + kz);
+                        double v0 = (double)k[base];
+                        ys[ky] = (nx == 2) ? (v0 + (double)k[base + 1]) / 2.0 : v0;
+                    }
+                    zs[kz] = (ny == 2) ? (ys[0] + ys[1]) / 2.0 : ys[0];
+                }
+                v = (nz == 2) ? (zs[0] + zs[1]) / 2.0 : zs[0];
+            }
+            Kc[(f * ndim + d) * C.nc + cc] = (T)v;
+        }
+    }
+}
+
+template <typename T>
+void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStream_t s) {
+    ++g_launch_count;
+    k_coarsen<T><<<nb(C.ncell), kBlock, 0, s>>>(nf, G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K, (T*)C.M,
+                                                (T*)C.K);
+}
+template void launch_coarsen<double>(const Grid&, int, const MGLevel&, MGLevel&, cudaStream_t);
+template void launch_coarsen<float>(const Grid&, int, const MGLevel&, MGLevel&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// transform in: r_V and the multigrid right-hand side
+// ---------------------------------------------------------------------------
+
+template <typename TV>
+__device__ __forceinline__ double rrho_at(const Grid& G, const double* L, const TV* v, double s, const Idx3& P,
+                                          int o0, int o1, int o2) {
+    int a = cell_map(P.i[0] + o0, G.n[0], G.bc[0]);
+    int b = cell_map(P.i[1] + o1, G.n[1], G.bc[1]);
+    int c = cell_map(P.i[2] + o2, G.n[2], G.bc[2]);
+    long long j = flat(G, a, b, c);
+    return L[j] * (s * (double)v[j]);
+}
+
+// r_u on face slot (pos + off along c); `up` selects the upper face of the cell
+template <typename TV>
+__device__ double ru_face(const Grid& G, const double* X, const double* L, const TV* v, double s, int c,
+                          const Idx3& P, bool up) {
+    const long long nc = G.ncell;
+    Idx3 Q = P;
+    if (up) {
+        if (G.bc[c] == 1 && P.i[c] + 1 == G.n[c]) return 0.0;
+        Q.i[c] = (P.i[c] + 1 == G.n[c]) ? 0 : P.i[c] + 1;
+    }
+    if (is_wall_slot(G, c, Q)) return 0.0;
+    long long j = flat(G, Q.i[0], Q.i[1], Q.i[2]);
+    int o[3] = {0, 0, 0};
+    o[c] = -1;
+    double rl = rrho_at(G, L, v, s, Q, o[0], o[1], o[2]);
+    double r0 = L[j] * (s * (double)v[j]);
+    double rb = 0.5 * (rl + r0);
+    double rho_l = load_cell(G, X, Q, o[0], o[1], o[2]);
+    double rho_f = 0.5 * (rho_l + X[j]);
+    double ruv = L[(2 + c) * nc + j] * (s * (double)v[(2 + c) * nc + j]);
+    double u = X[(2 + c) * nc + j];
+    return (ruv - u * rb) / rho_f;
+}
+
+template <typename TV, typename T>
+__global__ void k_precond_in(Grid G, const double* __restrict__ X, const double* __restrict__ L,
+                             const TV* __restrict__ v, const double* __restrict__ vscale, int vslot, double dt, int nf,
+                             T* __restrict__ rp, T* __restrict__ re, T* __restrict__ ru, T* __restrict__ rhs,
+                             T* __restrict__ x0) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= G.ncell) return;
+    const long long nc = G.ncell;
+    Idx3 P = decompose(G, cc);
+    const double s = vslot >= 0 ? vscale[vslot] : 1.0;
+    double rho = X[cc];
+    double E = X[nc + cc];
+    double r_rho = L[cc] * (s * (double)v[cc]);
+    double r_E = L[nc + cc] * (s * (double)v[nc + cc]);
+    double r_e = (r_E - E * r_rho) / rho;
+    double e = E;
+    if (G.energy_form == 1) {
+        double dot = 0.0, ke = 0.0;
+        for (int d = 0; d < G.ndim; ++d) {
+            const double* ud = X + (2 + d) * nc;
+            int o[3] = {0, 0, 0};
+            o[d] = 1;
+            double ul = load_normal(G, ud, d, P, 0, 0, 0);
+            double uu = load_normal(G, ud, d, P, o[0], o[1], o[2]);
+            double al = ru_face(G, X, L, v, s, d, P, false);
+            double au = ru_face(G, X, L, v, s, d, P, true);
+            dot = dot + 0.5 * (ul * al + uu * au);
+            ke = ke + 0.25 * (ul * ul + uu * uu);
+        }
+        r_e = r_e - dot;
+        e = E - ke;
+    }
+    for (int c = 0; c < G.ndim; ++c) ru[c * nc + cc] = (T)ru_face(G, X, L, v, s, c, P, false);
+    double dpdrho = G.gm1 * e;
+    double dpde = G.gm1 * rho;
+    double r_p = dpdrho * r_rho + dpde * r_e;
+    rp[cc] = (T)r_p;
+    re[cc] = (T)r_e;
+    double p = G.gm1 * rho * e;
+    Binv2 B = si_B(G, rho, p, dt, nf);
+    if (nf == 1) {
+        rhs[cc] = (T)(r_p / B.bpp);
+        x0[cc] = (T)0;
+    } else {
+        rhs[cc] = (T)(B.b00 * r_p + B.b01 * r_e);
+        rhs[nc + cc] = (T)(B.b10 * r_p + B.b11 * r_e);
+        x0[cc] = (T)0;
+        x0[nc + cc] = (T)0;
+    }
+}
+
+template <typename TV, typename T>
+void launch_precond_in(const Grid& G, const double* X, const double* L, const TV* v, const double* vscale, int vslot,
+                       double dt, int nf, T* rp, T* re, T* ru, MGLevel& L0, cudaStream_t s) {
+    ++g_launch_count;
+    k_precond_in<TV, T><<<nb(G.ncell), kBlock, 0, s>>>(G, X, L, v, vscale, vslot, dt, nf, rp, re, ru, (T*)L0.rhs,
+                                                      (T*)L0.x);
+}
+template void launch_precond_in<double, double>(const Grid&, const double*, const double*, const double*,
+                                                const double*, int, double, int, double*, double*, double*, MGLevel&,
+                                                cudaStream_t);
+template void launch_precond_in<float, float>(const Grid&, const double*, const double*, const float*, const double*,
+                                              int, double, int, float*, float*, float*, MGLevel&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// multigrid
+// ---------------------------------------------------------------------------
+
+template <typename T, int NF>
+__global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
+                         const T* __restrict__ rhs, int colour) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= Lv.nc) return;
+    int i[3];
+    i[0] = (int)(cc % Lv.n[0]);
+    long long t = cc / Lv.n[0];
+    i[1] = (int)(t % Lv.n[1]);
+    i[2] = (int)(t / Lv.n[1]);
+    if (((i[0] + i[1] + i[2]) & 1) != colour) return;
+    T dg[NF], of[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        dg[f] = (T)0;
+        of[f] = (T)0;
+        const T* xf = x + f * Lv.nc;
+        for (int d = 0; d < ndim; ++d) {
+            if (Lv.n[d] == 1) continue;
+            int up[3] = {i[0], i[1], i[2]}, dn[3] = {i[0], i[1], i[2]};
+            up[d] = wrapi(i[d] + 1, Lv.n[d]);
+            dn[d] = wrapi(i[d] - 1, Lv.n[d]);
+            long long ju = lflat(Lv, up[0], up[1], up[2]), jd = lflat(Lv, dn[0], dn[1], dn[2]);
+            const T* Kd = K + (f * ndim + d) * Lv.nc;
+            T Kl = Kd[cc], Ku = Kd[ju];
+            T ih2 = (T)Lv.ih2[d];
+            dg[f] = dg[f] + (Kl + Ku) * ih2;
+            of[f] = of[f] + (Ku * xf[ju] + Kl * xf[jd]) * ih2;
+        }
+    }
+    if (NF == 1) {
+        x[cc] = (rhs[cc] + of[0]) / (M[cc] + dg[0]);
+    } else {
+        T a11 = M[cc] + dg[0], a12 = M[Lv.nc + cc], a21 = M[2 * Lv.nc + cc], a22 = M[3 * Lv.nc + cc] + dg[NF - 1];
+        T b1 = rhs[cc] + of[0], b2 = rhs[Lv.nc + cc] + of[NF - 1];
+        T det = a11 * a22 - a12 * a21;
+        x[cc] = (a22 * b1 - a12 * b2) / det;
+        x[Lv.nc + cc] = (a11 * b2 - a21 * b1) / det;
+    }
+}
+
+template <typename T>
+void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s) {
+    ++g_launch_count;
+    if (nf == 1)
+        k_smooth<T, 1><<<nb(Lv.ncell), kBlock, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
+                                                       (const T*)Lv.rhs, colour);
+    else
+        k_smooth<T, 2><<<nb(Lv.ncell), kBlock, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
+                                                       (const T*)Lv.rhs, colour);
+}
+template void launch_smooth<double>(const Grid&, int, MGLevel&, int, cudaStream_t);
+template void launch_smooth<float>(const Grid&, int, MGLevel&, int, cudaStream_t);
+
+// residual rhs - A x at fine cell (a,b,c), field f
+template <typename T, int NF>
+__device__ __forceinline__ T fine_residual(int ndim, const LvlDev& F, const T* M, const T* K, const T* x, const T* rhs,
+                                           int f, int a, int b, int c) {
+    long long cc = lflat(F, a, b, c);
+    T out;
+    if (NF == 1) out = M[cc] * x[cc];
+    else out = M[(f * 2 + 0) * F.nc + cc] * x[cc] + M[(f * 2 + 1) * F.nc + cc] * x[F.nc + cc];
+    const T* xf = x + f * F.nc;
+    int i[3] = {a, b, c};
+    for (int d = 0; d < ndim; ++d) {
+        if (F.n[d] == 1) continue;
+        int up[3] = {a, b, c}, dn[3] = {a, b, c};
+        up[d] = wrapi(i[d] + 1, F.n[d]);
+        dn[d] = wrapi(i[d] - 1, F.n[d]);
+        long long ju = lflat(F, up[0], up[1], up[2]), jd = lflat(F, dn[0], dn[1], dn[2]);
+        const T* Kd = K + (f * ndim + d) * F.nc;
+        T Kl = Kd[cc], Ku = Kd[ju];
+        out = out - (Ku * (xf[ju] - xf[cc]) - Kl * (xf[cc] - xf[jd])) * (T)F.ih2[d];
+    }
+    return rhs[f * F.nc + cc] - out;
+}
+
+template <typename T, int NF>
+__global__ void k_restrict(int ndim, LvlDev F, LvlDev C, const T* __restrict__ M, const T* __restrict__ K,
+                           const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ rhsc,
+                           T* __restrict__ xc) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= C.nc) return;
+    int a = (int)(cc % C.n[0]);
+    long long t = cc / C.n[0];
+    int b = (int)(t % C.n[1]);
+    int c = (int)(t / C.n[1]);
+    int cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
+    int nx = cd[0] ? 2 : 1, ny = cd[1] ? 2 : 1, nz = cd[2] ? 2 : 1;
+    int x0 = cd[0] ? 2 * a : a, y0 = cd[1] ? 2 * b : b, z0 = cd[2] ? 2 * c : c;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        T zs[2];
+        for (int kz = 0; kz < nz; ++kz) {
+            T ys[2];
+            for (int ky = 0; ky < ny; ++ky) {
+                T v0 = fine_residual<T, NF>(ndim, F, M, K, x, rhs, f, x0, y0 + ky, z0 + kz);
+                ys[ky] = (nx == 2) ? (v0 + fine_residual<T, NF>(ndim, F, M, K, x, rhs, f, x0 + 1, y0 + ky, z0 + kz)) / (T)2
+                                   : v0;
+            }
+            zs[kz] = (ny == 2) ? (ys[0] + ys[1]) / (T)2 : ys[0];
+        }
+        rhsc[f * C.nc + cc] = (nz == 2) ? (zs[0] + zs[1]) / (T)2 : zs[0];
+        xc[f * C.nc + cc] = (T)0;
+    }
+}
+
+template <typename T>
+void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
+    ++g_launch_count;
+    if (nf == 1)
+        k_restrict<T, 1><<<nb(C.ncell), kBlock, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
+                                                       (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
+    else
+        k_restrict<T, 2><<<nb(C.ncell), kBlock, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
+                                                       (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
+}
+template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
+template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
+
+// coarse parents of fine index i along a coarsened direction
+__device__ __forceinline__ void parents(int i, int nc, int bc, int& par, int& oth) {
+    par = i >> 1;
+    oth = (i & 1) ? par + 1 : par - 1;
+    if (bc == 0) oth = wrapi(oth, nc);
+    else if (oth < 0 || oth >= nc) oth = par;
+}
+
+template <typename T, int NF>
+__global__ void k_prolong(int ndim, int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
+                          T* __restrict__ xf) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= F.nc) return;
+    int i[3];
+    i[0] = (int)(cc % F.n[0]);
+    long long t = cc / F.n[0];
+    i[1] = (int)(t % F.n[1]);
+    i[2] = (int)(t / F.n[1]);
+    int bc[3] = {bc0, bc1, bc2};
+    int pa[3], ot[3], cd[3];
+    for (int d = 0; d < 3; ++d) {
+        cd[d] = F.n[d] != C.n[d];
+        if (cd[d]) parents(i[d], C.n[d], bc[d], pa[d], ot[d]);
+        else { pa[d] = i[d]; ot[d] = i[d]; }
+    }
+    const T w0 = (T)0.75, w1 = (T)0.25;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T* q = xc + f * C.nc;
+        T vz[2];
+        int nz = cd[2] ? 2 : 1, ny = cd[1] ? 2 : 1;
+        for (int kz = 0; kz < nz; ++kz) {
+            int zz = kz == 0 ? pa[2] : ot[2];
+            T vy[2];
+            for (int ky = 0; ky < ny; ++ky) {
+                int yy = ky == 0 ? pa[1] : ot[1];
+                T a = q[lflat(C, pa[0], yy, zz)];
+                vy[ky] = cd[0] ? w0 * a + w1 * q[lflat(C, ot[0], yy, zz)] : a;
+            }
+            vz[kz] = cd[1] ? w0 * vy[0] + w1 * vy[1] : vy[0];
+        }
+        T v = cd[2] ? w0 * vz[0] + w1 * vz[1] : vz[0];
+        xf[f * F.nc + cc] = xf[f * F.nc + cc] + v;
+    }
+}
+
+template <typename T>
+void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
+    ++g_launch_count;
+    if (nf == 1)
+        k_prolong<T, 1><<<nb(F.ncell), kBlock, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
+                                                      (const T*)C.x, (T*)F.x);
+    else
+        k_prolong<T, 2><<<nb(F.ncell), kBlock, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
+                                                      (const T*)C.x, (T*)F.x);
+}
+template void launch_prolong<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
+template void launch_prolong<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
+
+template <typename T>
+__global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict__ rhs, T* __restrict__ x) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (nf == 1) {
+        x[0] = rhs[0] / M[0];
+    } else {
+        T a11 = M[0], a12 = M[1], a21 = M[2], a22 = M[3];
+        T det = a11 * a22 - a12 * a21;
+        x[0] = (a22 * rhs[0] - a12 * rhs[1]) / det;
+        x[1] = (a11 * rhs[1] - a21 * rhs[0]) / det;
+    }
+}
+
+template <typename T>
+void launch_coarsest(int nf, MGLevel& C, cudaStream_t s) {
+    ++g_launch_count;
+    k_coarsest<T><<<1, 32, 0, s>>>(nf, (const T*)C.M, (const T*)C.rhs, (T*)C.x);
+}
+template void launch_coarsest<double>(int, MGLevel&, cudaStream_t);
+template void launch_coarsest<float>(int, MGLevel&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// back substitution and transform out
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ double du_face(const Grid& G, const double* X, double dt, const T* ru, const T* dp, int c,
+                                          const Idx3& P, bool up) {
+    Idx3 Q = P;
+    if (up) {
+        if (G.bc[c] == 1 && P.i[c] + 1 == G.n[c]) return 0.0;
+        Q.i[c] = (P.i[c] + 1 == G.n[c]) ? 0 : P.i[c] + 1;
+    }
+    if (is_wall_slot(G, c, Q)) return 0.0;
+    const long long j = flat(G, Q.i[0], Q.i[1], Q.i[2]);
+    int o[3] = {0, 0, 0};
+    o[c] = -1;
+    int a = cell_map(Q.i[0] + o[0], G.n[0], G.bc[0]);
+    int b = cell_map(Q.i[1] + o[1], G.n[1], G.bc[1]);
+    int cz = cell_map(Q.i[2] + o[2], G.n[2], G.bc[2]);
+    long long jl = flat(G, a, b, cz);
+    double gp = ((double)dp[j] - (double)dp[jl]) * G.idx[c];
+    double rho_f = 0.5 * (X[jl] + X[j]);
+    return dt * ((double)ru[c * G.ncell + j] - G.theta * gp / rho_f);
+}
+
+template <typename T, typename TO>
+__global__ void k_precond_out(Grid G, const double* __restrict__ X, const double* __restrict__ Rinv, double dt, int nf,
+                              const T* __restrict__ rp, const T* __restrict__ re, const T* __restrict__ ru,
+                              const T* __restrict__ x, TO* __restrict__ z, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (cc < G.ncell) {
+        const long long nc = G.ncell;
+        Idx3 P = decompose(G, cc);
+        double rho = X[cc];
+        double E = X[nc + cc];
+        double e = E;
+        double dp = (double)x[cc];
+        double de;
+        if (nf == 1) de = dt * ((double)re[cc] + (dp / dt - (double)rp[cc]) / (G.gamma * rho));
+        else de = (double)x[nc + cc];
+        double dE = de;
+        if (G.energy_form == 1) {
+            double dot = 0.0, ke = 0.0;
+            for (int d = 0; d < G.ndim; ++d) {
+                const double* ud = X + (2 + d) * nc;
+                int o[3] = {0, 0, 0};
+                o[d] = 1;
+                double ul = load_normal(G, ud, d, P, 0, 0, 0);
+                double uu = load_normal(G, ud, d, P, o[0], o[1], o[2]);
+                double al = du_face<T>(G, X, dt, ru, x, d, P, false);
+                double au = du_face<T>(G, X, dt, ru, x, d, P, true);
+                dot = dot + 0.5 * (ul * al + uu * au);
+                ke = ke + 0.25 * (ul * ul + uu * uu);
+            }
+            dE = de + dot;
+            e = E - ke;
+        }
+        double dpdrho = G.gm1 * e;
+        double dpde = G.gm1 * rho;
+        double drho = (dp - dpde * de) / dpdrho;
+        double out[5];
+        out[0] = drho;
+        out[1] = dE;
+        for (int c = 0; c < G.ndim; ++c) out[2 + c] = du_face<T>(G, X, dt, ru, x, c, P, false);
+        for (int k = 0; k < 2 + G.ndim; ++k) {
+            long long j = k * nc + cc;
+            TO zv = (TO)(out[k] * Rinv[j]);
+            z[j] = zv;
+            double zd = (double)zv;
+            acc += zd * zd;
+        }
+    }
+    double s = block_sum<kBlock>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T, typename TO>
+void launch_precond_out(const Grid& G, const double* X, const double* Rinv, double dt, int nf, const T* rp,
+                        const T* re, const T* ru, const MGLevel& L0, TO* z, double* partials, cudaStream_t s) {
+    ++g_launch_count;
+    k_precond_out<T, TO><<<nb(G.ncell), kBlock, 0, s>>>(G, X, Rinv, dt, nf, rp, re, ru, (const T*)L0.x, z, partials);
+}
+template void launch_precond_out<double, double>(const Grid&, const double*, const double*, double, int, const double*,
+                                                 const double*, const double*, const MGLevel&, double*, double*,
+                                                 cudaStream_t);
+template void launch_precond_out<float, float>(const Grid&, const double*, const double*, double, int, const float*,
+                                               const float*, const float*, const MGLevel&, float*, double*,
+                                               cudaStream_t);
+
+}  // namespace jfnk

@@ -1,0 +1,432 @@
+// Finite-volume right-hand side R_U(X) of the paper's Sect. 2 on the
+// staggered grid, and the residual-type operators built from it:
+//   G(X)  = U(X)/dt - theta R_U(X)                 (Jv, Newton set-up)
+//   b^n   = U(X^n)/dt + (1-theta) R_U(X^n)          (Eq. crank_nicholson)
+//   F_U   = G(X) - b^n
+//   Jv    = L^-1 [G(X + delta R v) - G(X)] / delta   (Eqs. jacobian_free, pert_old)
+//
+// The evaluation is split so that every van Leer slope and every flux is
+// computed once per slot (the FP64 rate of sm_103a, about 0.6 TFMA/s, binds
+// these kernels, not HBM):
+//   k_eos          p, T per cell (perturbed state written first by k_perturb)
+//   k_face_fluxes  mass flux Fm_d and energy flux FE_d (advective part minus
+//                  conduction) on the lower face of every cell, per direction
+//   k_mom_fluxes   momentum fluxes Psi_cd: for c == d at cell centres, for
+//                  c != d on the edges between faces
+//   k_assemble     divergences, sources, U(X) and the requested combination
+//
+// Reconstruction (van Leer 1974): slope 2ab/(a+b) if ab > 0 else 0; the
+// upwind face value is q_L + s_L/2 when the upwinding speed is >= 0, else
+// q_R - s_R/2.  Only the slope on the upwind side is evaluated.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace jfnk {
+
+long long g_launch_count = 0;
+
+template <typename TZ>
+__global__ void k_perturb(Grid G, const double* __restrict__ X, const TZ* __restrict__ z,
+                          const double* __restrict__ R, const double* __restrict__ scal, int delta_slot,
+                          double* __restrict__ Xp, long long nvec) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= nvec) return;
+    const double delta = scal[delta_slot];
+    Xp[k] = X[k] + delta * (R[k] * (double)z[k]);
+}
+
+__global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__ p, double* __restrict__ T) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= G.ncell) return;
+    const long long nc = G.ncell;
+    double rho = X[c];
+    double e = X[nc + c];
+    if (G.energy_form == 1) {
+        Idx3 P = decompose(G, c);
+        double ke = 0.0;
+        for (int d = 0; d < G.ndim; ++d) {
+            const double* u = X + (2 + d) * nc;
+            int o[3] = {0, 0, 0};
+            o[d] = 1;
+            double ul = load_normal(G, u, d, P, 0, 0, 0);
+            double uu = load_normal(G, u, d, P, o[0], o[1], o[2]);
+            ke = ke + 0.25 * (ul * ul + uu * uu);
+        }
+        e = e - ke;
+    }
+    p[c] = G.gm1 * rho * e;
+    T[c] = G.gm1 * e;
+}
+
+__device__ __forceinline__ double conductivity(const Grid& G, double T) {
+    return G.chi_exp == 3.0 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+}
+
+__global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ p,
+                              const double* __restrict__ T, double* __restrict__ Fm, double* __restrict__ FE) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= G.ncell) return;
+    const long long nc = G.ncell;
+    Idx3 P = decompose(G, c);
+    const double* rho = X;
+    const double* E = X + nc;
+    for (int d = 0; d < G.ndim; ++d) {
+        int o[3] = {0, 0, 0};
+        const double u = load_normal(G, X + (2 + d) * nc, d, P, 0, 0, 0);
+        double rho_up, E_up;
+        if (u >= 0.0) {
+            o[d] = -2; double r2 = load_cell(G, rho, P, o[0], o[1], o[2]); double e2 = load_cell(G, E, P, o[0], o[1], o[2]);
+            o[d] = -1; double r1 = load_cell(G, rho, P, o[0], o[1], o[2]); double e1 = load_cell(G, E, P, o[0], o[1], o[2]);
+            double r0 = __ldg(rho + c), e0 = __ldg(E + c);
+            double sr = vanleer(r1 - r2, r0 - r1);
+            double se = vanleer(e1 - e2, e0 - e1);
+            rho_up = r1 + 0.5 * sr;
+            E_up = e1 + 0.5 * se;
+        } else {
+            o[d] = -1; double r1 = load_cell(G, rho, P, o[0], o[1], o[2]); double e1 = load_cell(G, E, P, o[0], o[1], o[2]);
+            o[d] = 1;  double r3 = load_cell(G, rho, P, o[0], o[1], o[2]); double e3 = load_cell(G, E, P, o[0], o[1], o[2]);
+            double r0 = __ldg(rho + c), e0 = __ldg(E + c);
+            double sr = vanleer(r0 - r1, r3 - r0);
+            double se = vanleer(e0 - e1, e3 - e0);
+            rho_up = r0 - 0.5 * sr;
+            E_up = e0 - 0.5 * se;
+        }
+        double fm = u * rho_up;
+        double fe = fm * E_up;
+        o[d] = -1;
+        if (G.energy_form == 1) {
+            double pl = load_cell(G, p, P, o[0], o[1], o[2]);
+            fe = fe + 0.5 * (pl + __ldg(p + c)) * u;
+        }
+        if (G.K0 != 0.0) {
+            double Tl = load_cell(G, T, P, o[0], o[1], o[2]);
+            double Tc = __ldg(T + c);
+            double q = 0.5 * (conductivity(G, Tl) + conductivity(G, Tc)) * (Tc - Tl) * G.idx[d];
+            fe = fe - q;
+        }
+        Fm[d * nc + c] = fm;
+        FE[d * nc + c] = fe;
+    }
+}
+
+// Fm_d at slot (pos + off) where the offset is along a direction in which Fm_d
+// behaves as a cell quantity (any direction other than d).
+__device__ __forceinline__ double load_Fm_cell(const Grid& G, const double* Fm_d, const Idx3& P, int o0, int o1, int o2) {
+    return load_cell(G, Fm_d, P, o0, o1, o2);
+}
+
+// Fm_d at the upper face (slot + 1 along d): zero at an upper wall.
+__device__ __forceinline__ double load_face_up(const Grid& G, const double* f, int d, const Idx3& P) {
+    if (G.bc[d] == 1 && P.i[d] + 1 == G.n[d]) return 0.0;
+    int o[3] = {0, 0, 0};
+    o[d] = 1;
+    return load_cell(G, f, P, o[0], o[1], o[2]);
+}
+
+__global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ Fm,
+                             double* __restrict__ Psi) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= G.ncell) return;
+    const long long nc = G.ncell;
+    Idx3 P = decompose(G, cc);
+    const int nd = G.ndim;
+    for (int c = 0; c < nd; ++c) {
+        const double* uc = X + (2 + c) * nc;
+        for (int d = 0; d < nd; ++d) {
+            double psi;
+            if (c == d) {
+                // flux at the cell centre between faces i and i+1 along c
+                double m = 0.5 * (__ldg(Fm + c * nc + cc) + load_face_up(G, Fm + c * nc, c, P));
+                int o[3] = {0, 0, 0};
+                double uup;
+                if (m >= 0.0) {
+                    o[c] = -1; double um = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
+                    o[c] = 1;  double up = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    uup = u0 + 0.5 * vanleer(u0 - um, up - u0);
+                } else {
+                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
+                    o[c] = 1;  double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    o[c] = 2;  double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    uup = u1 - 0.5 * vanleer(u1 - u0, u2 - u1);
+                }
+                psi = m * uup;
+            } else {
+                // flux on the edge between c-face i_c and d-face i_d
+                int o[3] = {0, 0, 0};
+                o[c] = -1;
+                double m = 0.5 * (load_Fm_cell(G, Fm + d * nc, P, o[0], o[1], o[2]) + __ldg(Fm + d * nc + cc));
+                o[c] = 0;
+                double uup;
+                if (m >= 0.0) {
+                    o[d] = -2; double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    o[d] = -1; double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
+                    uup = u1 + 0.5 * vanleer(u1 - u2, u0 - u1);
+                } else {
+                    o[d] = -1; double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
+                    o[d] = 1;  double u3 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                    uup = u0 - 0.5 * vanleer(u0 - u1, u3 - u0);
+                }
+                psi = m * uup;
+            }
+            Psi[(c * nd + d) * nc + cc] = psi;
+        }
+    }
+}
+
+template <int MODE, typename TO>
+__global__ void k_assemble(Grid G, const double* __restrict__ X, const double* __restrict__ p,
+                           const double* __restrict__ Fm, const double* __restrict__ FE,
+                           const double* __restrict__ Psi, const double* __restrict__ bn,
+                           const double* __restrict__ G0, const double* __restrict__ Linv,
+                           const double* __restrict__ scal, int delta_slot, double dt_inv,
+                           double* __restrict__ outd, TO* __restrict__ outb) {
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cc >= G.ncell) return;
+    const long long nc = G.ncell;
+    const int nd = G.ndim;
+    Idx3 P = decompose(G, cc);
+    const double th = G.theta;
+    double inv_delta = 0.0;
+    if (MODE == kModeJv) inv_delta = 1.0 / scal[delta_slot];
+
+    double Rr = 0.0, RE = 0.0, divu = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        const double* fmd = Fm + d * nc;
+        const double* fed = FE + d * nc;
+        double fm0 = __ldg(fmd + cc), fm1 = load_face_up(G, fmd, d, P);
+        double fe0 = __ldg(fed + cc), fe1 = load_face_up(G, fed, d, P);
+        Rr = Rr - (fm1 - fm0) * G.idx[d];
+        RE = RE - (fe1 - fe0) * G.idx[d];
+        if (G.energy_form == 0) {
+            const double* ud = X + (2 + d) * nc;
+            double u0 = load_normal(G, ud, d, P, 0, 0, 0);
+            int o[3] = {0, 0, 0};
+            o[d] = 1;
+            double u1 = load_normal(G, ud, d, P, o[0], o[1], o[2]);
+            divu = divu + (u1 - u0) * G.idx[d];
+        } else if (G.g[d] != 0.0) {
+            RE = RE + G.g[d] * 0.5 * (fm0 + fm1);
+        }
+    }
+    const double pc = __ldg(p + cc);
+    if (G.energy_form == 0) RE = RE - pc * divu;
+
+    const double rho = __ldg(X + cc);
+    double Uv[5], Rv[5];
+    Uv[0] = rho;            Rv[0] = Rr;
+    Uv[1] = rho * __ldg(X + nc + cc); Rv[1] = RE;
+    for (int c = 0; c < nd; ++c) {
+        if (is_wall_slot(G, c, P)) { Uv[2 + c] = 0.0; Rv[2 + c] = 0.0; continue; }
+        int o[3] = {0, 0, 0};
+        o[c] = -1;
+        double pl = load_cell(G, p, P, o[0], o[1], o[2]);
+        double rl = load_cell(G, X, P, o[0], o[1], o[2]);
+        double rho_f = 0.5 * (rl + rho);
+        double Rc = -(pc - pl) * G.idx[c];
+        if (G.g[c] != 0.0) Rc = Rc + rho_f * G.g[c];
+        for (int d = 0; d < nd; ++d) {
+            const double* ps = Psi + (c * nd + d) * nc;
+            double a, b;
+            if (c == d) {
+                b = __ldg(ps + cc);
+                a = load_cell(G, ps, P, o[0], o[1], o[2]);      // centre i-1 along c
+                Rc = Rc - (b - a) * G.idx[c];
+            } else {
+                a = __ldg(ps + cc);
+                b = load_face_up(G, ps, d, P);
+                Rc = Rc - (b - a) * G.idx[d];
+            }
+        }
+        Uv[2 + c] = rho_f * __ldg(X + (2 + c) * nc + cc);
+        Rv[2 + c] = Rc;
+    }
+    for (int k = 0; k < 2 + nd; ++k) {
+        const long long j = k * nc + cc;
+        const bool wall = (k >= 2) && is_wall_slot(G, k - 2, P);
+        if (MODE == kModeG) {
+            outd[j] = Uv[k] * dt_inv - th * Rv[k];
+        } else if (MODE == kModeBn) {
+            outd[j] = Uv[k] * dt_inv + (1.0 - th) * Rv[k];
+        } else if (MODE == kModeRes) {
+            outd[j] = Uv[k] * dt_inv - th * Rv[k] - bn[j];
+        } else if (MODE == kModeNewton) {
+            double g = Uv[k] * dt_inv - th * Rv[k];
+            outd[j] = g;
+            outb[j] = wall ? (TO)0 : (TO)(-((g - bn[j]) * Linv[j]));
+        } else {  // kModeJv
+            double g = Uv[k] * dt_inv - th * Rv[k];
+            outb[j] = wall ? (TO)0 : (TO)((g - G0[j]) * inv_delta * Linv[j]);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// scaling L, R (Eq. jacobian_system_norm) and ||R^-1 X||^2 partial sums
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ double internal_e(const Grid& G, const double* X, const Idx3& P, int o0, int o1, int o2) {
+    const long long nc = G.ncell;
+    double E = load_cell(G, X + nc, P, o0, o1, o2);
+    if (G.energy_form == 0) return E;
+    Idx3 Q;
+    Q.i[0] = cell_map(P.i[0] + o0, G.n[0], G.bc[0]);
+    Q.i[1] = cell_map(P.i[1] + o1, G.n[1], G.bc[1]);
+    Q.i[2] = cell_map(P.i[2] + o2, G.n[2], G.bc[2]);
+    double ke = 0.0;
+    for (int d = 0; d < G.ndim; ++d) {
+        const double* u = X + (2 + d) * nc;
+        int o[3] = {0, 0, 0};
+        o[d] = 1;
+        double ul = load_normal(G, u, d, Q, 0, 0, 0);
+        double uu = load_normal(G, u, d, Q, o[0], o[1], o[2]);
+        ke = ke + 0.25 * (ul * ul + uu * uu);
+    }
+    return E - ke;
+}
+
+__global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, double alpha2,
+                          double* __restrict__ L, double* __restrict__ R, double* __restrict__ Linv,
+                          double* __restrict__ Rinv, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (cc < G.ncell) {
+        const long long nc = G.ncell;
+        Idx3 P = decompose(G, cc);
+        double rho = X[cc], E = X[nc + cc];
+        double Lv[5], Rv[5];
+        Lv[0] = rho; Rv[0] = rho;
+        Lv[1] = rho * E; Rv[1] = E;
+        double e0 = internal_e(G, X, P, 0, 0, 0);
+        double cs0 = sqrt(G.gamma * G.gm1 * e0);
+        for (int c = 0; c < G.ndim; ++c) {
+            if (is_wall_slot(G, c, P)) { Lv[2 + c] = 1.0; Rv[2 + c] = 1.0; continue; }
+            int o[3] = {0, 0, 0};
+            o[c] = -1;
+            double rl = load_cell(G, X, P, o[0], o[1], o[2]);
+            double el = internal_e(G, X, P, o[0], o[1], o[2]);
+            double csl = sqrt(G.gamma * G.gm1 * el);
+            double rho_f = 0.5 * (rl + rho);
+            double cs_f = 0.5 * (csl + cs0);
+            double au = fabs(X[(2 + c) * nc + cc]);
+            Lv[2 + c] = rho_f * fmax(au, alpha1 * cs_f);
+            Rv[2 + c] = fmax(au, alpha2 * cs_f);
+        }
+        for (int k = 0; k < 2 + G.ndim; ++k) {
+            long long j = k * nc + cc;
+            L[j] = Lv[k];
+            R[j] = Rv[k];
+            Linv[j] = 1.0 / Lv[k];
+            Rinv[j] = 1.0 / Rv[k];
+            double xh = X[j] / Rv[k];
+            if (k >= 2 && is_wall_slot(G, k - 2, P)) xh = 0.0;
+            acc += xh * xh;
+        }
+    }
+    double s = block_sum<kBlock>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// max over cells of |u_cell| + c_s (Sect. 1, CFL_hydro)
+__global__ void k_signal_speed(Grid G, const double* __restrict__ X, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (cc < G.ncell) {
+        const long long nc = G.ncell;
+        Idx3 P = decompose(G, cc);
+        double s = 0.0;
+        for (int c = 0; c < G.ndim; ++c) {
+            int o[3] = {0, 0, 0};
+            o[c] = 1;
+            double u0 = load_normal(G, X + (2 + c) * nc, c, P, 0, 0, 0);
+            double u1 = load_normal(G, X + (2 + c) * nc, c, P, o[0], o[1], o[2]);
+            double ub = 0.5 * (u0 + u1);
+            s = s + ub * ub;
+        }
+        double e = internal_e(G, X, P, 0, 0, 0);
+        v = sqrt(s) + sqrt(G.gamma * G.gm1 * e);
+        if (!(v == v)) v = __longlong_as_double(0x7ff8000000000000ULL);
+    }
+    double m = block_max<kBlock>(v, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+
+static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+void launch_eos(const Grid& G, const double* X, double* p, double* T, cudaStream_t s) {
+    ++g_launch_count;
+    k_eos<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, p, T);
+}
+
+template <typename TZ>
+void launch_perturb(const Grid& G, const double* X, const TZ* z, const double* R, const double* scal, int slot,
+                    double* Xp, cudaStream_t s) {
+    long long nvec = (2 + G.ndim) * G.ncell;
+    ++g_launch_count;
+    k_perturb<TZ><<<nblk(nvec), kBlock, 0, s>>>(G, X, z, R, scal, slot, Xp, nvec);
+}
+template void launch_perturb<double>(const Grid&, const double*, const double*, const double*, const double*, int,
+                                     double*, cudaStream_t);
+template void launch_perturb<float>(const Grid&, const double*, const float*, const double*, const double*, int,
+                                    double*, cudaStream_t);
+
+void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
+                        cudaStream_t s) {
+    ++g_launch_count;
+    k_face_fluxes<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, p, T, Fm, FE);
+}
+
+void launch_mom_fluxes(const Grid& G, const double* X, const double* Fm, double* Psi, cudaStream_t s) {
+    ++g_launch_count;
+    k_mom_fluxes<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, Fm, Psi);
+}
+
+void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
+                   double* Psi, cudaStream_t s) {
+    launch_face_fluxes(G, X, p, T, Fm, FE, s);
+    launch_mom_fluxes(G, X, Fm, Psi, s);
+}
+
+template <int MODE, typename TO>
+void launch_assemble(const Grid& G, const double* X, const double* p, const double* Fm, const double* FE,
+                     const double* Psi, const double* bn, const double* G0, const double* Linv, const double* scal,
+                     int slot, double dt, double* outd, TO* outb, cudaStream_t s) {
+    ++g_launch_count;
+    k_assemble<MODE, TO><<<nblk(G.ncell), kBlock, 0, s>>>(G, X, p, Fm, FE, Psi, bn, G0, Linv, scal, slot, 1.0 / dt,
+                                                         outd, outb);
+}
+#define INST(M, T)                                                                                             \
+    template void launch_assemble<M, T>(const Grid&, const double*, const double*, const double*, const double*, \
+                                        const double*, const double*, const double*, const double*,           \
+                                        const double*, int, double, double*, T*, cudaStream_t);
+INST(kModeG, double)
+INST(kModeBn, double)
+INST(kModeRes, double)
+INST(kModeNewton, double)
+INST(kModeNewton, float)
+INST(kModeJv, double)
+INST(kModeJv, float)
+#undef INST
+
+void launch_scaling(const Grid& G, const double* X, double a1, double a2, double* L, double* R, double* Linv,
+                    double* Rinv, double* partials, cudaStream_t s) {
+    ++g_launch_count;
+    k_scaling<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, a1, a2, L, R, Linv, Rinv, partials);
+}
+
+void launch_signal_speed(const Grid& G, const double* X, double* partials, cudaStream_t s) {
+    ++g_launch_count;
+    k_signal_speed<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, partials);
+}
+
+unsigned cell_blocks(const Grid& G) { return nblk(G.ncell); }
+
+}  // namespace jfnk

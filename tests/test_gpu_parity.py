@@ -1,0 +1,261 @@
+"""Parity of the CUDA library with the float64 CPU oracle (same seeded inputs).
+
+Tolerances: the benchmark spec's bound for FP64 mode is 1e-10 relative, normwise
+in scaled space.  Where the paper's finite-difference Jv has a noise floor
+(eps_machine |G| / (delta |Jv|)), parity is asserted at lambda = 1e-4 and only
+bounded at lambda = 1e-7.  Elementwise checks use |gpu - ref| <= rtol |ref| +
+atol * max|ref| per field."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import discretization as D
+from oracle import jfnk as J
+from oracle import precond as PC
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def jf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_03662_gb300 import build
+    build.build()
+    import paper_1512_03662_gb300 as jf
+    return jf
+
+
+def _dev(x):
+    return torch.as_tensor(np.asarray(x), dtype=torch.float64).cuda()
+
+
+def _cpu(t):
+    return t.detach().double().cpu()
+
+
+def _relnorm(a, b, w=None):
+    a, b = _cpu(a), torch.as_tensor(b).double()
+    if w is not None:
+        a, b = a / w, b / w
+    return float((a - b).norm() / b.norm())
+
+
+def _case(cid, n, form=0, seed=7, rel=0.02, vel=0.1, cfl=None, mach=None):
+    kw = {"n": n}
+    if mach is not None:
+        kw["mach"] = mach
+    wl = W.config(cid, **kw)
+    wl.energy_form = form
+    P = D.Problem.from_workload(wl)
+    Xn = torch.as_tensor(wl.X0).clone()
+    if form == D.ENERGY_TOTAL:
+        Xn[P.ncell:2 * P.ncell] += 0.5 * float(Xn[2 * P.ncell:].abs().max()) ** 2 + 1.0
+    pert = torch.as_tensor(W.random_vector(wl, seed))
+    scale = torch.cat([Xn[:2 * P.ncell].abs() * rel,
+                       torch.full((P.ndim * P.ncell,), vel, dtype=torch.float64) *
+                       float(torch.sqrt(wl.gamma * (wl.gamma - 1) * Xn[P.ncell:2 * P.ncell]).mean())])
+    X = Xn + pert * scale
+    dt = D.cfl_dt(P, Xn, wl.cfl_hydro if cfl is None else cfl)
+    return wl, P, X, Xn, dt
+
+
+def _solver(jf, wl, **kw):
+    """Solver for the workload; grids that are not powers of two (ragged
+    tails) run without the multigrid preconditioner."""
+    pow2 = all((v & (v - 1)) == 0 for v in wl.n[:wl.ndim])
+    kw.setdefault("theta", wl.theta)
+    kw.setdefault("precond", wl.precond if pow2 else 0)
+    return jf.Solver.from_workload(wl, jf.default_options(**kw))
+
+
+CASES = [(1, (64, 64), 0), (1, (32, 32), 1), (2, (32, 32), 0), (2, (20, 12), 0), (3, (16, 16, 16), 1),
+         (4, (16, 16, 16), 0), (4, (12, 10, 6), 1)]
+
+
+@pytest.mark.parametrize("cid,n,form", CASES)
+def test_residual_parity(jf, cid, n, form):
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    S = _solver(jf, wl)
+    F = S.residual(_dev(X), _dev(Xn), dt)
+    Fo = D.residual(P, X, Xn, dt)
+    sc = J.scaling(P, X, J.Options())
+    assert _relnorm(F, Fo, sc.L) < 1e-10
+    Fg = _cpu(F)
+    for k in range(P.nfield):
+        a, b = Fg[k * P.ncell:(k + 1) * P.ncell], Fo[k * P.ncell:(k + 1) * P.ncell]
+        assert float((a - b).abs().max()) <= 1e-9 * float(b.abs().max()) + 1e-300, k
+
+
+@pytest.mark.parametrize("cid,n,form", CASES)
+def test_scaling_parity(jf, cid, n, form):
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    S = _solver(jf, wl)
+    L, R, xn = S.scaling(_dev(X))
+    sc = J.scaling(P, X, J.Options())
+    assert _relnorm(L, sc.L) < 1e-14
+    assert _relnorm(R, sc.R) < 1e-14
+    assert xn == pytest.approx(sc.xhat_norm, rel=1e-13)
+
+
+@pytest.mark.parametrize("cid,n,form", CASES)
+def test_jv_parity(jf, cid, n, form):
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    v = torch.as_tensor(W.random_vector(wl, 3))
+    for lam, tol in ((1e-4, 1e-10), (1e-7, 1e-6)):
+        S = _solver(jf, wl, lam=lam)
+        Jv, delta = S.jv(_dev(X), dt, _dev(v))
+        oo = J.Options(lam=lam)
+        sc = J.scaling(P, X, oo)
+        Jo, do = J.jv(P, X, D.G_operator(P, X, dt), sc, v, dt, oo)
+        assert delta == pytest.approx(do, rel=1e-13)
+        assert _relnorm(Jv, Jo) < tol, (lam, _relnorm(Jv, Jo))
+
+
+PC_CASES = [(1, (64, 64), 0, 1), (1, (32, 32), 1, 1), (2, (32, 32), 0, 2), (2, (16, 16), 0, 1),
+            (4, (16, 16, 16), 0, 2), (4, (8, 8, 8), 1, 2), (3, (16, 16, 16), 0, 1)]
+
+
+@pytest.mark.parametrize("cid,n,form,pc", PC_CASES)
+def test_precond_parity(jf, cid, n, form, pc):
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    v = torch.as_tensor(W.random_vector(wl, 5))
+    o = jf.default_options(theta=wl.theta, precond=pc, mg_cycles=2)
+    S = jf.Solver.from_workload(wl, o)
+    w = S.precond_apply(_dev(X), dt, _dev(v))
+    oo = J.Options(precond=pc, mg_cycles=2)
+    si = PC.setup(P, X, dt, oo)
+    wo = PC.apply(si, v, J.scaling(P, X, oo))
+    assert _relnorm(w, wo) < 1e-10
+    # wall slots stay zero
+    for c in range(P.ndim):
+        if wl.bc[c] == W.BC_WALL:
+            f = _cpu(w)[(2 + c) * P.ncell:(3 + c) * P.ncell].reshape(P.shape)
+            idx = [slice(None)] * 3
+            idx[2 - c] = 0
+            assert float(f[tuple(idx)].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("cid,n,pc,m,its", [(1, (32, 32), 1, 8, 12), (2, (32, 32), 2, 10, 10),
+                                           (4, (8, 8, 8), 2, 6, 9), (1, (16, 16), 0, 5, 7)])
+def test_linear_solve_parity_fixed_iterations(jf, cid, n, pc, m, its):
+    """One Newton linear solve with a fixed iteration count (restarts
+    included when its > m): the GMRES correction matches the oracle's."""
+    wl, P, X, Xn, dt = _case(cid, n, 0, cfl=5.0)
+    o = jf.default_options(theta=wl.theta, precond=pc, gmres_m=m, gmres_max_it=its, fixed_iterations=1, lam=1e-4)
+    S = jf.Solver.from_workload(wl, o)
+    dx, st, _ = S.linear_solve(_dev(X), _dev(Xn), dt)
+    oo = J.Options(precond=pc, gmres_m=m, gmres_max_it=its, fixed_iterations=True, lam=1e-4)
+    sc = J.scaling(P, X, oo)
+    G0 = D.G_operator(P, X, dt)
+    Fhat = (G0 - D.bn_constant(P, Xn, dt)) / sc.L
+    Minv = (lambda v: PC.apply(PC.setup(P, X, dt, oo), v, sc)) if pc else (lambda v: v)
+    si = PC.setup(P, X, dt, oo) if pc else None
+    if pc:
+        Minv = lambda v: PC.apply(si, v, sc)       # noqa: E731
+    dxo, sto = J.gmres(lambda z: J.jv(P, X, G0, sc, z, dt, oo)[0], Minv, -Fhat, oo.eta, m, its, 0, True)
+    assert st["gmres_iterations"][0] == sto.iterations
+    assert _relnorm(dx, dxo) < 1e-9, _relnorm(dx, dxo)
+
+
+def test_step_parity_fixed_iterations(jf):
+    wl, P, X, Xn, dt = _case(1, (32, 32), 0, cfl=10.0)
+    o = jf.default_options(theta=wl.theta, precond=1, gmres_m=10, gmres_max_it=10, newton_max=3,
+                           fixed_iterations=1, lam=1e-4)
+    S = jf.Solver.from_workload(wl, o)
+    Xg = _dev(Xn)
+    st = S.step(Xg, dt)
+    assert st["newton_iterations"] == 3
+    oo = J.Options(precond=1, gmres_m=10, gmres_max_it=10, newton_max=3, fixed_iterations=True, lam=1e-4)
+    Xo, sto = J.newton_step(P, Xn, dt, oo)
+    sc = J.scaling(P, Xn, oo)
+    assert _relnorm(Xg - _dev(Xn), Xo - Xn, sc.R) < 1e-8
+
+
+@pytest.mark.parametrize("cid,n", [(1, (64, 64)), (2, (32, 32)), (4, (16, 16, 16))])
+def test_step_tolerance_mode(jf, cid, n):
+    """Each side converges on its own to newton_tol = 1e-8: the steps agree
+    to a small multiple of the tolerance (scaled infinity norm)."""
+    wl = W.config(cid, n=n)
+    P = D.Problem.from_workload(wl)
+    cfl = wl.cfl_hydro * (n[0] / 256.0 if cid == 4 else 1.0)
+    dt = D.cfl_dt(P, wl.X0, cfl)
+    S = jf.Solver.from_workload(wl)
+    Xg = _dev(wl.X0)
+    st = S.step(Xg, dt, 1e-8, 1e-4)
+    assert st["converged"], st
+    Xo, sto = J.newton_step(P, wl.X0, dt, J.Options(precond=wl.precond))
+    assert sto.converged
+    sc = J.scaling(P, Xo, J.Options())
+    err = float(((_cpu(Xg) - Xo) / sc.R).abs().max())
+    assert err < 1e-6, (err, st["gmres_iterations"], sto.gmres_iterations)
+
+
+@pytest.mark.parametrize("cid,n", [(1, (64, 64)), (2, (32, 32)), (4, (16, 16, 16))])
+def test_mixed_precision_step_error(jf, cid, n):
+    """FP32 Krylov basis + FP32 preconditioner: the converged step agrees with
+    the FP64 oracle to the Newton tolerance level."""
+    wl = W.config(cid, n=n)
+    P = D.Problem.from_workload(wl)
+    cfl = wl.cfl_hydro * (n[0] / 256.0 if cid == 4 else 1.0)
+    dt = D.cfl_dt(P, wl.X0, cfl)
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=jf.MIXED)
+    S = jf.Solver.from_workload(wl, o)
+    Xg = _dev(wl.X0)
+    st = S.step(Xg, dt, 1e-8, 1e-4)
+    assert st["converged"], st
+    Xo, _ = J.newton_step(P, wl.X0, dt, J.Options(precond=wl.precond))
+    sc = J.scaling(P, Xo, J.Options())
+    err = float(((_cpu(Xg) - Xo) / sc.R).abs().max())
+    assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("cid,n,form", CASES)
+def test_dt_from_cfl_parity(jf, cid, n, form):
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    S = _solver(jf, wl)
+    assert S.dt_from_cfl(_dev(X), 7.0) == pytest.approx(D.cfl_dt(P, X, 7.0), rel=1e-14)
+
+
+def test_zero_rhs_gives_zero_correction(jf):
+    """A uniform state at rest is steady: F = 0, the linear solve returns 0
+    without dividing by ||F|| = 0."""
+    wl = W.config(1, n=(16, 16))
+    shape = (1, 16, 16)
+    f = [np.full(shape, v) for v in (1.0, 2.0, 0.0, 0.0)]
+    X = torch.as_tensor(np.concatenate([a.ravel() for a in f]))
+    S = jf.Solver.from_workload(wl)
+    dx, st, code = S.linear_solve(_dev(X), _dev(X), 0.01)
+    assert code == 0 and float(dx.abs().max()) == 0.0
+
+
+def test_invalid_arguments_are_rejected(jf):
+    wl = W.config(1, n=(16, 16))
+    with pytest.raises(jf.JFNKError) as e:
+        jf.Solver(2, (3, 16, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), 5 / 3)
+    assert e.value.status == jf.JFNK_EINVAL
+    with pytest.raises(jf.JFNKError):
+        jf.Solver(2, (24, 16, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), 5 / 3)   # MG needs powers of two
+    with pytest.raises(jf.JFNKError):
+        jf.Solver(2, (16, 16, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), 1.0)
+    S = jf.Solver.from_workload(wl)
+    X = _dev(wl.X0)
+    with pytest.raises(jf.JFNKError):
+        S.residual(X, X, -1.0)
+    # the same grid without preconditioning accepts non-powers of two
+    S2 = jf.Solver(2, (24, 16, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), 5 / 3,
+                   options=jf.default_options(precond=0))
+    assert S2.nvec == 4 * 24 * 16
+
+
+def test_nonfinite_state_is_reported(jf):
+    wl = W.config(1, n=(16, 16))
+    X = torch.as_tensor(wl.X0).clone()
+    X[5] = float("nan")
+    S = jf.Solver.from_workload(wl)
+    with pytest.raises(jf.JFNKError) as e:
+        S.step(_dev(X), 1e-3)
+    assert e.value.status == jf.JFNK_ENONFINITE
