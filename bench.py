@@ -38,17 +38,25 @@ UNIT = "implicit steps/s"
 NEWTON_TOL = 1e-8
 ETA = 1e-4
 
-# Executed FP64 floating-point operations per cell of one residual evaluation
-# inside Jv, per kernel (3D, internal energy, gravity, conduction), from the
-# ncu instruction counters (dadd + dmul + 2 dfma) of a 64^3 capture divided
-# by the cell count; division and square-root sequences are included as the
-# DFMA/DMUL/DADD instructions they execute.  See profiles/.
-FP64_FLOPS_PER_CELL = {"perturb": 10.0, "eos": 3.0, "face_fluxes": 185.0, "mom_fluxes": 420.0, "assemble": 100.0}
+# FP64 work per cell of one residual evaluation inside Jv, per kernel (3D,
+# internal energy, gravity, conduction, FP32 Krylov vectors), measured with
+# the ncu thread-instruction counters of a 128^3 capture (profiles/
+# jv_kernels_128cubed.md): flops = dadd + dmul + 2 dfma, instructions =
+# dadd + dmul + dfma, both divided by the cell count.  Division sequences are
+# counted as the DFMA/DMUL/DADD instructions they execute.
+FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 3.0, "face_fluxes": 168.5, "mom_fluxes": 234.7, "assemble": 123.8}
+FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 3.0, "face_fluxes": 123.3, "mom_fluxes": 171.3, "assemble": 91.9}
+# DRAM bytes per cell per launch from the same capture (dram__bytes_read +
+# dram__bytes_write); at 128^3 part of the reads hit the 129 MB L2, so these
+# are lower bounds for 256^3 (where the algorithmic bytes below apply).
+DRAM_BYTES_PER_CELL_128 = {"perturb": 128.2, "eos": 16.2, "face_fluxes": 77.3, "mom_fluxes": 99.4,
+                           "assemble": 265.7}
 JV_KERNELS = ["perturb", "eos", "face_fluxes", "mom_fluxes", "assemble"]
 # Algorithmic HBM bytes per cell of one launch of each Jv kernel (3D, FP64
-# state; reads and writes of the arrays each kernel must touch once).
-HBM_BYTES_PER_CELL = {"perturb": 5 * 8 * 4, "eos": 2 * 8 + 2 * 8, "face_fluxes": 5 * 8 + 2 * 8 + 6 * 8,
-                      "mom_fluxes": 3 * 8 + 3 * 8 + 9 * 8, "assemble": 5 * 8 + 8 + 6 * 8 + 9 * 8 + 3 * 5 * 8}
+# state, FP32 Krylov vectors; each array the kernel must touch read or
+# written once).
+HBM_BYTES_PER_CELL = {"perturb": 5 * (8 + 4 + 8 + 8), "eos": 2 * 8 + 2 * 8, "face_fluxes": 5 * 8 + 2 * 8 + 6 * 8,
+                      "mom_fluxes": 3 * 8 + 3 * 8 + 9 * 8, "assemble": 5 * 8 + 8 + 6 * 8 + 9 * 8 + 5 * 8 * 2 + 5 * 4}
 
 
 def load_peaks():
@@ -60,10 +68,13 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-# FP64 FMA rate of this GPU model measured by a dependent-chain throughput
-# probe (8 independent DFMA chains per thread, 152x8 blocks of 256 threads):
-# 1.200 TFLOP/s (0.600 T DFMA/s); the nominal figure is 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.200
+# FP64 peak of GB300 from its unit counts and clock: ncu reports a sustained
+# peak of 2 FP64 thread instructions per cycle per SM; 152 SMs at the 2070 MHz
+# maximum SM clock give 0.629 T instructions/s, 1.26 TFLOP/s with an FMA
+# counted as two flops (the nominal figure is 1.25 TFLOP/s; a DFMA
+# throughput probe on this machine measured 1.20 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.258
+FP64_PEAK_TINST = 0.629
 
 
 class ClockSampler:
@@ -258,7 +269,8 @@ def kernel_main(args):
     stream = torch.cuda.Stream(device)
     wl = make_workload(args.n)
     prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
-    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec)
+    # a single Jv or preconditioner call needs no Krylov basis: restart length 1
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, gmres_m=1)
     S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
     X = torch.as_tensor(wl.X0, dtype=torch.float64, device=device)
     dt = S.dt_from_cfl(X, wl.cfl_hydro)
@@ -349,11 +361,17 @@ def main():
     per_launch_ms = kms[dom] / max(1, njv)
     flops = FP64_FLOPS_PER_CELL[name] * wl.ncell
     achieved_tflops = flops / (per_launch_ms / 1e3) / 1e12
+    tinst = FP64_INST_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e12
     hbm_gbs = HBM_BYTES_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e9
+    scale = wl.ncell / 128 ** 3
     roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_src": "measured FP64 DFMA probe", "hbm_gbs": hbm_gbs,
-                "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"]}
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                "traffic": DRAM_BYTES_PER_CELL_128[name] * 128 ** 3 * scale,
+                "traffic_note": "ncu DRAM bytes of a 128^3 launch scaled by the cell ratio",
+                "peak_src": "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "fp64_issue_tinst_s": tinst, "fp64_issue_frac": tinst / FP64_PEAK_TINST,
+                "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"],
+                "algorithmic_bytes_per_cell": HBM_BYTES_PER_CELL[name]}
 
     e2e = None
     if not args.no_e2e:

@@ -14,7 +14,7 @@ struct Grid {
     int ndim;
     int n[3];
     long long ncell;
-    double dx[3], idx[3], idx2[3];
+    double dx[3], idx[3], idx2[3], tidx[3];   // tidx = 2 / dx
     int bc[3];                       // 0 periodic, 1 wall
     double gamma, gm1;
     double g[3];
@@ -24,6 +24,38 @@ struct Grid {
 };
 
 struct Idx3 { int i[3]; };
+
+// Launch shape of the cell kernels: x along threadIdx.x (coalesced), y and
+// z from the grid, so no thread decomposes a flat index by division.
+struct CellLaunch {
+    dim3 grid, block;
+};
+
+inline CellLaunch cell_launch(const int n[3]) {
+    int bx = 32;
+    while (bx < n[0] && bx < 128) bx *= 2;
+    int by = 128 / bx;
+    CellLaunch L;
+    L.block = dim3(bx, by, 1);
+    L.grid = dim3((n[0] + bx - 1) / bx, (n[1] + by - 1) / by, n[2]);
+    return L;
+}
+
+// Position of this thread in a cell_launch grid; false outside the grid.
+__device__ __forceinline__ bool cell_pos(const int n[3], Idx3& P, long long& c) {
+    P.i[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    P.i[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    P.i[2] = blockIdx.z;
+    if (P.i[0] >= n[0] || P.i[1] >= n[1]) return false;
+    c = ((long long)P.i[2] * n[1] + P.i[1]) * n[0] + P.i[0];
+    return true;
+}
+
+__device__ __forceinline__ int block_linear() {
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+__device__ __forceinline__ int thread_linear() { return threadIdx.x + blockDim.x * threadIdx.y; }
 
 __device__ __forceinline__ Idx3 decompose(const Grid& G, long long c) {
     Idx3 r;
@@ -39,12 +71,11 @@ __device__ __forceinline__ long long flat(const Grid& G, int i0, int i1, int i2)
 }
 
 // Cell-quantity index of position k along a direction of size n: periodic
-// wrap, or mirror about the wall faces (k -> -k-1, k -> 2n-1-k).
+// wrap, or mirror about the wall faces (k -> -k-1, k -> 2n-1-k).  Stencil
+// offsets never exceed the grid size (n >= 4, |offset| <= 3), so one
+// conditional wrap replaces an integer modulo.
 __device__ __forceinline__ int cell_map(int k, int n, int bc) {
-    if (bc == 0) {
-        k %= n;
-        return k < 0 ? k + n : k;
-    }
+    if (bc == 0) return k < 0 ? k + n : (k >= n ? k - n : k);
     if (k < 0) return -k - 1;
     if (k >= n) return 2 * n - 1 - k;
     return k;
@@ -78,7 +109,9 @@ __device__ __forceinline__ double load_normal(const Grid& G, const double* __res
             k[d] = cell_map(k[d], G.n[d], G.bc[d]);
         }
     }
-    return sgn * __ldg(u + flat(G, k[0], k[1], k[2]));
+    double v = __ldg(u + flat(G, k[0], k[1], k[2]));
+    // sign flip on the sign bit (integer pipe) instead of an FP64 multiply
+    return sgn < 0.0 ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL) : v;
 }
 
 // True when slot p is the wall face of direction c.
@@ -92,16 +125,36 @@ __device__ __forceinline__ double vanleer(double a, double b) {
     return ab > 0.0 ? (2.0 * ab) / (a + b) : 0.0;
 }
 
+// Upwind reconstruction without divergent branches.  With q_near the cell
+// on the upwind side of the face, q_far its other neighbour and q_other the
+// cell across the face, the face value is
+//     q_near + s/2,   s = vanleer(q_near - q_far, q_other - q_near).
+// For the right-hand (negative speed) case this is q_R - s_R/2 exactly,
+// because the two differences change sign, which is exact, and s/2 =
+// ab/(a+b) exactly (scaling by two commutes with rounding).  The division
+// is executed by every thread (denominator 1 where the limiter is off) so
+// the warp does not split.
+__device__ __forceinline__ double upwind_value(double q_near, double q_far, double q_other) {
+    double a = q_near - q_far;
+    double b = q_other - q_near;
+    double ab = a * b;
+    bool pos = ab > 0.0;
+    double den = pos ? (a + b) : 1.0;
+    double half_s = ab / den;
+    return q_near + (pos ? half_s : 0.0);
+}
+
 template <typename T> struct Acc { typedef double type; };
 
 // Block-wide sum of one double per thread; result valid in thread 0.
 template <int BS>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int lane = t & 31, w = t >> 5;
     if (lane == 0) sh[w] = v;
     __syncthreads();
-    v = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+    v = (t < BS / 32) ? sh[t] : 0.0;
     if (w == 0) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     }
@@ -111,11 +164,12 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 template <int BS>
 __device__ __forceinline__ double block_max(double v, double* sh) {
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int lane = t & 31, w = t >> 5;
     if (lane == 0) sh[w] = v;
     __syncthreads();
-    v = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+    v = (t < BS / 32) ? sh[t] : 0.0;
     if (w == 0) {
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     }

@@ -36,7 +36,7 @@ struct jfnk_handle {
     // workspace carve-up
     double *bn, *G0, *L, *R, *Linv, *Rinv, *Xp, *dxh, *p, *T, *Fm, *FE, *Psi, *partials, *scal;
     double *H, *cs, *sn, *g, *y, *vscale, *hc2;
-    void *V, *Z, *rp, *re, *ru;
+    void *V, *Z, *rp, *re, *ru, *C;
     long long npartials;
     std::vector<MGLevel> levels;
     size_t elt;        // bytes per basis element
@@ -87,7 +87,7 @@ size_t plan(jfnk_handle* h, char* base) {
     h->Fm = (double*)take(nd * nc * 8);
     h->FE = (double*)take(nd * nc * 8);
     h->Psi = (double*)take((long long)nd * nd * nc * 8);
-    long long cb = (nc + kBlock - 1) / kBlock;
+    long long cb = cell_blocks(h->G);
     h->npartials = std::max<long long>(cb, (long long)kRedBlocks * (m + 1));
     h->partials = (double*)take(h->npartials * 8);
     h->scal = (double*)take(kNumSlots * 8);
@@ -105,6 +105,7 @@ size_t plan(jfnk_handle* h, char* base) {
         h->rp = take(nc * e);
         h->re = take(nc * e);
         h->ru = take(nd * nc * e);
+        h->C = take((size_t)PcNumFields * nc * e);
         for (auto& L : h->levels) {
             L.M = take((size_t)h->nf * h->nf * L.ncell * e);
             L.K = take((size_t)h->nf * nd * L.ncell * e);
@@ -177,10 +178,11 @@ T* Vcol(jfnk_handle* h, int j) { return (T*)h->V + (long long)j * h->nvec; }
 template <typename T>
 T* Zcol(jfnk_handle* h, int j) { return (T*)h->Z + (long long)j * h->nvec; }
 
+// coefficients of the preconditioner at X (needs the scaling of X)
 void si_setup(jfnk_handle* h, const double* X, double dt) {
     if (h->nf == 0) return;
-    if (h->mixed) launch_si_setup<float>(h->G, X, dt, h->nf, h->levels[0], h->stream);
-    else launch_si_setup<double>(h->G, X, dt, h->nf, h->levels[0], h->stream);
+    if (h->mixed) launch_pc_setup<float>(h->G, X, h->L, h->Rinv, dt, h->nf, (float*)h->C, h->levels[0], h->stream);
+    else launch_pc_setup<double>(h->G, X, h->L, h->Rinv, dt, h->nf, (double*)h->C, h->levels[0], h->stream);
     for (size_t l = 0; l + 1 < h->levels.size(); ++l) {
         if (h->mixed) launch_coarsen<float>(h->G, h->nf, h->levels[l], h->levels[l + 1], h->stream);
         else launch_coarsen<double>(h->G, h->nf, h->levels[l], h->levels[l + 1], h->stream);
@@ -219,11 +221,12 @@ void precond(jfnk_handle* h, const double* X, double dt, const T* v, int vslot, 
         launch_finalize(h->partials, kRedBlocks, h->scal, kSlotZnorm, 0, s);
         return;
     }
-    launch_precond_in<T, T>(h->G, X, h->L, v, h->vscale, vslot, dt, h->nf, (T*)h->rp, (T*)h->re, (T*)h->ru,
-                            h->levels[0], s);
+    (void)X;
+    launch_precond_in<T>(h->G, (const T*)h->C, v, h->vscale, vslot, h->nf, (T*)h->rp, (T*)h->re, (T*)h->ru,
+                         h->levels[0], s);
     for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<T>(h, 0);
-    launch_precond_out<T, T>(h->G, X, h->Rinv, dt, h->nf, (const T*)h->rp, (const T*)h->re, (const T*)h->ru,
-                             h->levels[0], z, h->partials, s);
+    launch_precond_out<T>(h->G, (const T*)h->C, dt, h->nf, (const T*)h->rp, (const T*)h->re, (const T*)h->ru,
+                          h->levels[0], z, h->partials, s);
     launch_finalize(h->partials, (int)cblocks(h), h->scal, kSlotZnorm, 0, s);
 }
 
@@ -462,6 +465,7 @@ jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_g
         }
         G.idx[d] = 1.0 / G.dx[d];
         G.idx2[d] = G.idx[d] * G.idx[d];
+        G.tidx[d] = 2.0 * G.idx[d];
     }
     G.ncell = (long long)G.n[0] * G.n[1] * G.n[2];
     if (!(eos->gamma > 1.0)) { *out = h; return fail(h, JFNK_EINVAL, "gamma must exceed 1"); }

@@ -91,13 +91,26 @@ struct MGLevel {
     void* rhs;   // nf fields
 };
 
+// per-cell coefficient fields of the preconditioner transforms
+// PcQ0..PcQ5: FP64 mode: B^-1 entries (b00, b01, b10, b11) applied to
+// (r_p, r_e) as the oracle does; FP32 mode: the same map folded with the
+// transform, rhs_p = Q0 r_rho + Q1 r_E - Q2 <u.r_u>, rhs_e = Q3 r_rho + Q4 r_E
+// - Q5 <u.r_u>, coefficients formed in double so no FP32 cancellation occurs.
+enum {
+    PcLr = 0, PcLE, PcInvRho, PcE, PcDpdrho, PcDpde, PcInvDpdrho, PcCde,
+    PcQ0, PcQ1, PcQ2, PcQ3, PcQ4, PcQ5, PcPr, PcPE, PcRinvR, PcRinvE,
+    PcLu, PcU = PcLu + 3, PcInvRhof = PcU + 3, PcThf = PcInvRhof + 3, PcRinvU = PcThf + 3,
+    PcNumFields = PcRinvU + 3
+};
+
 template <typename T>
-void launch_si_setup(const Grid& G, const double* X, double dt, int nf, MGLevel& L0, cudaStream_t s);
+void launch_pc_setup(const Grid& G, const double* X, const double* L, const double* Rinv, double dt, int nf, T* C,
+                     MGLevel& L0, cudaStream_t s);
 template <typename T>
 void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStream_t s);
-template <typename TV, typename T>
-void launch_precond_in(const Grid& G, const double* X, const double* L, const TV* v, const double* vscale, int vslot,
-                       double dt, int nf, T* rp, T* re, T* ru, MGLevel& L0, cudaStream_t s);
+template <typename T>
+void launch_precond_in(const Grid& G, const T* C, const T* v, const double* vscale, int vslot, int nf, T* rp, T* re,
+                       T* ru, MGLevel& L0, cudaStream_t s);
 template <typename T>
 void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s);
 template <typename T>
@@ -106,8 +119,8 @@ template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
 template <typename T>
 void launch_coarsest(int nf, MGLevel& C, cudaStream_t s);
-template <typename T, typename TO>
-void launch_precond_out(const Grid& G, const double* X, const double* Rinv, double dt, int nf, const T* rp,
-                        const T* re, const T* ru, const MGLevel& L0, TO* z, double* partials, cudaStream_t s);
+template <typename T>
+void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
+                        const MGLevel& L0, T* z, double* partials, cudaStream_t s);
 
 }  // namespace jfnk

@@ -14,6 +14,30 @@
 
 namespace jfnk {
 
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) used by
+// the float basis: a dot product accumulated as an unevaluated pair
+// (sum, err) is as accurate as one accumulated in twice the working
+// precision (Ogita, Rump & Oishi, "Accurate sum and dot product", 2005),
+// without touching the FP64 pipe inside the loop.
+struct CompF {
+    float s, e;
+};
+
+// (explicitly rounded intrinsics: the compiler must not contract these into FMAs)
+__device__ __forceinline__ void comp_add(CompF& a, float p) {
+    float t = __fadd_rn(a.s, p);
+    float bp = __fsub_rn(t, a.s);
+    a.e = __fadd_rn(a.e, __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+    a.s = t;
+}
+
+__device__ __forceinline__ void comp_fma(CompF& a, float x, float y) {
+    float p = __fmul_rn(x, y);
+    float err = fmaf(x, y, -p);
+    comp_add(a, p);
+    a.e = __fadd_rn(a.e, err);
+}
+
 __global__ void k_finalize(const double* __restrict__ partials, int n, double* scal, int slot, int op) {
     __shared__ double sh[32];
     double v = (op == 2) ? 0.0 : 0.0;
@@ -110,6 +134,26 @@ __global__ void k_multidot(const T* __restrict__ V, long long ld, const T* __res
     }
 }
 
+// float basis: compensated FP32 accumulation per thread, double per block
+template <int NV>
+__global__ void k_multidot_f32(const float* __restrict__ V, long long ld, const float* __restrict__ w, long long n,
+                               double* __restrict__ partials) {
+    __shared__ double sh[32];
+    CompF acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = CompF{0.f, 0.f};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        float wk = w[k];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) comp_fma(acc[i], V[i * ld + k], wk);
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = block_sum<kBlock>((double)acc[i].s + (double)acc[i].e, sh);
+        if (threadIdx.x == 0) partials[blockIdx.x * NV + i] = s;
+    }
+}
+
 // generic fallback for any count: loops over groups of 8
 template <typename T>
 __global__ void k_multidot_group(const T* __restrict__ V, long long ld, int i0, int ni, int nvtot,
@@ -132,6 +176,19 @@ __global__ void k_multidot_group(const T* __restrict__ V, long long ld, int i0, 
 
 template <typename T>
 void launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s) {
+    if (sizeof(T) == 4 && nv <= 32) {
+        const float* Vf = (const float*)V;
+        const float* wf = (const float*)w;
+        ++g_launch_count;
+        switch (nv) {
+#define CASEF(N) case N: k_multidot_f32<N><<<kRedBlocks, kBlock, 0, s>>>(Vf, ld, wf, n, partials); return;
+            CASEF(1) CASEF(2) CASEF(3) CASEF(4) CASEF(5) CASEF(6) CASEF(7) CASEF(8)
+            CASEF(9) CASEF(10) CASEF(11) CASEF(12) CASEF(13) CASEF(14) CASEF(15) CASEF(16)
+            CASEF(17) CASEF(18) CASEF(19) CASEF(20) CASEF(21) CASEF(22) CASEF(23) CASEF(24)
+            CASEF(25) CASEF(26) CASEF(27) CASEF(28) CASEF(29) CASEF(30) CASEF(31) CASEF(32)
+#undef CASEF
+        }
+    }
     switch (nv) {
 #define CASE(N) case N: ++g_launch_count; k_multidot<T, N><<<kRedBlocks, kBlock, 0, s>>>(V, ld, w, n, partials); return;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
@@ -211,9 +268,54 @@ __global__ void k_axpy_norm_dyn(T* __restrict__ w, const T* __restrict__ V, long
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// float basis: w -= sum_i c_i v_i with c_i split into float hi + lo parts and
+// the sum kept as a compensated pair; ||w||^2 of the rounded result, compensated.
+template <int NV>
+__global__ void k_axpy_norm_f32(float* __restrict__ w, const float* __restrict__ V, long long ld,
+                                const double* __restrict__ hcol, const double* __restrict__ vscale, long long n,
+                                double* __restrict__ partials) {
+    __shared__ double sh[32];
+    __shared__ float chi[32], clo[32];
+    if (threadIdx.x < NV) {
+        double c = -(hcol[threadIdx.x] * vscale[threadIdx.x]);
+        float h = (float)c;
+        chi[threadIdx.x] = h;
+        clo[threadIdx.x] = (float)(c - (double)h);
+    }
+    __syncthreads();
+    CompF nrm{0.f, 0.f};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        CompF x{w[k], 0.f};
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            float v = V[i * ld + k];
+            comp_fma(x, chi[i], v);
+            x.e = fmaf(clo[i], v, x.e);
+        }
+        float xs = x.s + x.e;
+        w[k] = xs;
+        comp_fma(nrm, xs, xs);
+    }
+    double s = block_sum<kBlock>((double)nrm.s + (double)nrm.e, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 template <typename T>
 void launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
                       double* partials, cudaStream_t s) {
+    if (sizeof(T) == 4 && nv <= 32) {
+        float* wf = (float*)w;
+        const float* Vf = (const float*)V;
+        ++g_launch_count;
+        switch (nv) {
+#define CASEF(N) case N: k_axpy_norm_f32<N><<<kRedBlocks, kBlock, 0, s>>>(wf, Vf, ld, hcol, vscale, n, partials); return;
+            CASEF(1) CASEF(2) CASEF(3) CASEF(4) CASEF(5) CASEF(6) CASEF(7) CASEF(8)
+            CASEF(9) CASEF(10) CASEF(11) CASEF(12) CASEF(13) CASEF(14) CASEF(15) CASEF(16)
+            CASEF(17) CASEF(18) CASEF(19) CASEF(20) CASEF(21) CASEF(22) CASEF(23) CASEF(24)
+            CASEF(25) CASEF(26) CASEF(27) CASEF(28) CASEF(29) CASEF(30) CASEF(31) CASEF(32)
+#undef CASEF
+        }
+    }
     switch (nv) {
 #define CASE(N) case N: ++g_launch_count; k_axpy_norm<T, N><<<kRedBlocks, kBlock, 0, s>>>(w, V, ld, hcol, vscale, n, partials); return;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)

@@ -30,14 +30,19 @@ struct LvlDev {
     int n[3];
     long long nc;
     double ih2[3];
+    float ih2f[3];   // the same in float, so FP32 kernels convert nothing
 };
 
 static inline LvlDev lvl(const MGLevel& L) {
     LvlDev d;
-    for (int i = 0; i < 3; ++i) { d.n[i] = L.n[i]; d.ih2[i] = L.ih2[i]; }
+    for (int i = 0; i < 3; ++i) { d.n[i] = L.n[i]; d.ih2[i] = L.ih2[i]; d.ih2f[i] = (float)L.ih2[i]; }
     d.nc = L.ncell;
     return d;
 }
+
+template <typename T> __device__ __forceinline__ T ih2_of(const LvlDev& L, int d);
+template <> __device__ __forceinline__ double ih2_of<double>(const LvlDev& L, int d) { return L.ih2[d]; }
+template <> __device__ __forceinline__ float ih2_of<float>(const LvlDev& L, int d) { return L.ih2f[d]; }
 
 __device__ __forceinline__ long long lflat(const LvlDev& L, int a, int b, int c) {
     return ((long long)c * L.n[1] + b) * L.n[0] + a;
@@ -50,7 +55,7 @@ __device__ __forceinline__ double conductivity_si(const Grid& G, double T) {
 }
 
 // ---------------------------------------------------------------------------
-// coefficients at the current iterate
+// coefficients at the current iterate (once per Newton iteration)
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double e_internal_at(const Grid& G, const double* X, const Idx3& P, int o0, int o1, int o2) {
@@ -94,14 +99,20 @@ __device__ __forceinline__ Binv2 si_B(const Grid& G, double rho, double p, doubl
     return B;
 }
 
-template <typename T>
-__global__ void k_si_setup(Grid G, const double* __restrict__ X, double dt, int nf, T* __restrict__ M,
-                           T* __restrict__ K) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= G.ncell) return;
+
+// Per-cell coefficient fields of the transforms, in the basis precision T.
+// Field order (index * ncell): see PcField.  All divisions of the
+// preconditioner happen here, once per Newton iteration.
+template <int ND, typename T>
+__global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* __restrict__ L,
+                           const double* __restrict__ Rinv, double dt, int nf, T* __restrict__ C,
+                           T* __restrict__ M, T* __restrict__ K) {
+    Idx3 P;
+    long long cc;
+    if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
-    Idx3 P = decompose(G, cc);
     double rho = X[cc];
+    double E = X[nc + cc];
     double e = e_internal_at(G, X, P, 0, 0, 0);
     double p = G.gm1 * rho * e;
     Binv2 B = si_B(G, rho, p, dt, nf);
@@ -115,32 +126,96 @@ __global__ void k_si_setup(Grid G, const double* __restrict__ X, double dt, int 
     }
     const double cv = 1.0 / G.gm1;
     const double chi0 = (G.K0 != 0.0) ? conductivity_si(G, G.gm1 * e) : 0.0;
-    for (int c = 0; c < G.ndim; ++c) {
-        double m = (is_wall_slot(G, c, P) || G.n[c] == 1) ? 0.0 : 1.0;
+    double dpdrho = G.gm1 * e, dpde = G.gm1 * rho;
+    C[PcLr * nc + cc] = (T)L[cc];
+    C[PcLE * nc + cc] = (T)L[nc + cc];
+    C[PcInvRho * nc + cc] = (T)(1.0 / rho);
+    C[PcE * nc + cc] = (T)E;
+    C[PcDpdrho * nc + cc] = (T)dpdrho;
+    C[PcDpde * nc + cc] = (T)dpde;
+    C[PcInvDpdrho * nc + cc] = (T)(1.0 / dpdrho);
+    C[PcCde * nc + cc] = (T)(1.0 / (G.gamma * rho));
+    // r_p = Pr r_rho + PE r_E - dpde <u.r_u>: first row of dV/dU in the
+    // product form printed in Sect. 3.2 (no cancellation between terms)
+    const double Pr = dpdrho - dpde * E / rho, PE = dpde / rho;
+    C[PcPr * nc + cc] = (T)Pr;
+    C[PcPE * nc + cc] = (T)PE;
+    if (sizeof(T) == 8) {
+        if (nf == 1) {
+            C[PcQ0 * nc + cc] = (T)(1.0 / B.bpp);
+        } else {
+            C[PcQ0 * nc + cc] = (T)B.b00;
+            C[PcQ1 * nc + cc] = (T)B.b01;
+            C[PcQ2 * nc + cc] = (T)B.b10;
+            C[PcQ3 * nc + cc] = (T)B.b11;
+        }
+    } else {
+        // rhs = B^-1 (r_p, r_e) with r_e = (r_E - E r_rho)/rho - <u.r_u>
+        double b00, b01, b10, b11;
+        if (nf == 1) { b00 = 1.0 / B.bpp; b01 = 0.0; b10 = 0.0; b11 = 0.0; }
+        else { b00 = B.b00; b01 = B.b01; b10 = B.b10; b11 = B.b11; }
+        C[PcQ0 * nc + cc] = (T)(b00 * Pr - b01 * E / rho);
+        C[PcQ1 * nc + cc] = (T)(b00 * PE + b01 / rho);
+        C[PcQ2 * nc + cc] = (T)(b00 * dpde + b01);
+        C[PcQ3 * nc + cc] = (T)(b10 * Pr - b11 * E / rho);
+        C[PcQ4 * nc + cc] = (T)(b10 * PE + b11 / rho);
+        C[PcQ5 * nc + cc] = (T)(b10 * dpde + b11);
+    }
+    C[PcRinvR * nc + cc] = (T)Rinv[cc];
+    C[PcRinvE * nc + cc] = (T)Rinv[nc + cc];
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+        const bool wall = is_wall_slot(G, c, P);
+        double m = (wall || G.n[c] == 1) ? 0.0 : 1.0;
         int o[3] = {0, 0, 0};
         o[c] = -1;
         double rl = load_cell(G, X, P, o[0], o[1], o[2]);
         double rho_f = 0.5 * (rl + rho);
-        K[(0 * G.ndim + c) * nc + cc] = (T)(m / rho_f);
+        K[(0 * ND + c) * nc + cc] = (T)(m / rho_f);
         if (nf == 2) {
             double chil = 0.0;
             if (G.K0 != 0.0) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
-            K[(1 * G.ndim + c) * nc + cc] = (T)(m * (0.5 * (chil + chi0)) / cv);
+            K[(1 * ND + c) * nc + cc] = (T)(m * (0.5 * (chil + chi0)) / cv);
         }
+        const double u = wall ? 0.0 : X[(2 + c) * nc + cc];
+        C[(PcLu + c) * nc + cc] = (T)L[(2 + c) * nc + cc];
+        C[(PcU + c) * nc + cc] = (T)u;
+        C[(PcInvRhof + c) * nc + cc] = (T)(wall ? 0.0 : 1.0 / rho_f);
+        C[(PcThf + c) * nc + cc] = (T)(wall ? 0.0 : G.theta * G.idx[c] / rho_f);
+        C[(PcRinvU + c) * nc + cc] = (T)Rinv[(2 + c) * nc + cc];
     }
 }
 
+#define CELL_LAUNCH_T(KERNEL, T, ...)                                                     \
+    do {                                                                                  \
+        CellLaunch cl_ = cell_launch(G.n);                                                \
+        ++g_launch_count;                                                                 \
+        if (G.ndim == 3) KERNEL<3, T><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);        \
+        else KERNEL<2, T><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);                    \
+    } while (0)
+
 template <typename T>
-void launch_si_setup(const Grid& G, const double* X, double dt, int nf, MGLevel& L0, cudaStream_t s) {
-    ++g_launch_count;
-    k_si_setup<T><<<nb(G.ncell), kBlock, 0, s>>>(G, X, dt, nf, (T*)L0.M, (T*)L0.K);
+void launch_pc_setup(const Grid& G, const double* X, const double* L, const double* Rinv, double dt, int nf, T* C,
+                     MGLevel& L0, cudaStream_t s) {
+    CELL_LAUNCH_T(k_pc_setup, T, G, X, L, Rinv, dt, nf, C, (T*)L0.M, (T*)L0.K);
 }
-template void launch_si_setup<double>(const Grid&, const double*, double, int, MGLevel&, cudaStream_t);
-template void launch_si_setup<float>(const Grid&, const double*, double, int, MGLevel&, cudaStream_t);
+template void launch_pc_setup<double>(const Grid&, const double*, const double*, const double*, double, int, double*,
+                                      MGLevel&, cudaStream_t);
+template void launch_pc_setup<float>(const Grid&, const double*, const double*, const double*, double, int, float*,
+                                     MGLevel&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // coarse coefficients
 // ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool lvl_pos(const LvlDev& L, int i[3], long long& c) {
+    i[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    i[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    i[2] = blockIdx.z;
+    if (i[0] >= L.n[0] || i[1] >= L.n[1]) return false;
+    c = lflat(L, i[0], i[1], i[2]);
+    return true;
+}
 
 // mean over the children of coarse cell (a,b,c), pairs along x, then y, then z
 template <typename T>
@@ -163,12 +238,10 @@ __device__ __forceinline__ double child_mean(const T* f, const LvlDev& F, const 
 template <typename T>
 __global__ void k_coarsen(int nf, int ndim, LvlDev F, LvlDev C, const T* __restrict__ Mf, const T* __restrict__ Kf,
                           T* __restrict__ Mc, T* __restrict__ Kc) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= C.nc) return;
-    int a = (int)(cc % C.n[0]);
-    long long t = cc / C.n[0];
-    int b = (int)(t % C.n[1]);
-    int c = (int)(t / C.n[1]);
+    int ic[3];
+    long long cc;
+    if (!lvl_pos(C, ic, cc)) return;
+    const int a = ic[0], b = ic[1], c = ic[2];
     int cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
     for (int q = 0; q < nf * nf; ++q) Mc[q * C.nc + cc] = (T)child_mean(Mf + q * F.nc, F, cd, a, b, c);
     for (int f = 0; f < nf; ++f) {
@@ -179,9 +252,7 @@ __global__ void k_coarsen(int nf, int ndim, LvlDev F, LvlDev C, const T* __restr
                 // fine lower faces of the even children along d, mean over the other coarsened dims
                 int cd2[3] = {cd[0], cd[1], cd[2]};
                 cd2[d] = 0;
-                int pos[3] = {a, b, c};
                 int fx = cd[0] ? 2 * a : a, fy = cd[1] ? 2 * b : b, fz = cd[2] ? 2 * c : c;
-                (void)pos;
                 int nx = cd2[0] ? 2 : 1, ny = cd2[1] ? 2 : 1, nz = cd2[2] ? 2 : 1;
                 double zs[2];
                 for (int kz = 0; kz < nz; ++kz) {
@@ -202,9 +273,10 @@ __global__ void k_coarsen(int nf, int ndim, LvlDev F, LvlDev C, const T* __restr
 
 template <typename T>
 void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStream_t s) {
+    CellLaunch cl = cell_launch(C.n);
     ++g_launch_count;
-    k_coarsen<T><<<nb(C.ncell), kBlock, 0, s>>>(nf, G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K, (T*)C.M,
-                                                (T*)C.K);
+    k_coarsen<T><<<cl.grid, cl.block, 0, s>>>(nf, G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K, (T*)C.M,
+                                              (T*)C.K);
 }
 template void launch_coarsen<double>(const Grid&, int, const MGLevel&, MGLevel&, cudaStream_t);
 template void launch_coarsen<float>(const Grid&, int, const MGLevel&, MGLevel&, cudaStream_t);
@@ -213,119 +285,117 @@ template void launch_coarsen<float>(const Grid&, int, const MGLevel&, MGLevel&, 
 // transform in: r_V and the multigrid right-hand side
 // ---------------------------------------------------------------------------
 
-template <typename TV>
-__device__ __forceinline__ double rrho_at(const Grid& G, const double* L, const TV* v, double s, const Idx3& P,
-                                          int o0, int o1, int o2) {
+// r_rho at the cell (pos + off) with ghost mapping
+template <typename T, typename TV>
+__device__ __forceinline__ T rrho_at(const Grid& G, const T* C, const TV* v, T s, const Idx3& P, int o0, int o1,
+                                     int o2) {
     int a = cell_map(P.i[0] + o0, G.n[0], G.bc[0]);
     int b = cell_map(P.i[1] + o1, G.n[1], G.bc[1]);
     int c = cell_map(P.i[2] + o2, G.n[2], G.bc[2]);
     long long j = flat(G, a, b, c);
-    return L[j] * (s * (double)v[j]);
+    return C[PcLr * G.ncell + j] * (s * (T)v[j]);
 }
 
-// r_u on face slot (pos + off along c); `up` selects the upper face of the cell
-template <typename TV>
-__device__ double ru_face(const Grid& G, const double* X, const double* L, const TV* v, double s, int c,
-                          const Idx3& P, bool up) {
+// r_u on the lower face of cell Q in direction c (zero at a wall slot)
+template <typename T, typename TV>
+__device__ __forceinline__ T ru_at(const Grid& G, const T* C, const TV* v, T s, int c, const Idx3& Q) {
     const long long nc = G.ncell;
-    Idx3 Q = P;
-    if (up) {
-        if (G.bc[c] == 1 && P.i[c] + 1 == G.n[c]) return 0.0;
-        Q.i[c] = (P.i[c] + 1 == G.n[c]) ? 0 : P.i[c] + 1;
-    }
-    if (is_wall_slot(G, c, Q)) return 0.0;
-    long long j = flat(G, Q.i[0], Q.i[1], Q.i[2]);
+    const long long j = flat(G, Q.i[0], Q.i[1], Q.i[2]);
     int o[3] = {0, 0, 0};
     o[c] = -1;
-    double rl = rrho_at(G, L, v, s, Q, o[0], o[1], o[2]);
-    double r0 = L[j] * (s * (double)v[j]);
-    double rb = 0.5 * (rl + r0);
-    double rho_l = load_cell(G, X, Q, o[0], o[1], o[2]);
-    double rho_f = 0.5 * (rho_l + X[j]);
-    double ruv = L[(2 + c) * nc + j] * (s * (double)v[(2 + c) * nc + j]);
-    double u = X[(2 + c) * nc + j];
-    return (ruv - u * rb) / rho_f;
+    T rl = rrho_at<T, TV>(G, C, v, s, Q, o[0], o[1], o[2]);
+    T r0 = C[PcLr * nc + j] * (s * (T)v[j]);
+    T rb = (T)0.5 * (rl + r0);
+    T ruv = C[(PcLu + c) * nc + j] * (s * (T)v[(2 + c) * nc + j]);
+    return (ruv - C[(PcU + c) * nc + j] * rb) * C[(PcInvRhof + c) * nc + j];
 }
 
-template <typename TV, typename T>
-__global__ void k_precond_in(Grid G, const double* __restrict__ X, const double* __restrict__ L,
-                             const TV* __restrict__ v, const double* __restrict__ vscale, int vslot, double dt, int nf,
-                             T* __restrict__ rp, T* __restrict__ re, T* __restrict__ ru, T* __restrict__ rhs,
-                             T* __restrict__ x0) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= G.ncell) return;
+template <int ND, typename T>
+__global__ void k_precond_in(Grid G, const T* __restrict__ C, const T* __restrict__ v,
+                             const double* __restrict__ vscale, int vslot, int nf, T* __restrict__ rp,
+                             T* __restrict__ re, T* __restrict__ ru, T* __restrict__ rhs, T* __restrict__ x0) {
+    Idx3 P;
+    long long cc;
+    if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
-    Idx3 P = decompose(G, cc);
-    const double s = vslot >= 0 ? vscale[vslot] : 1.0;
-    double rho = X[cc];
-    double E = X[nc + cc];
-    double r_rho = L[cc] * (s * (double)v[cc]);
-    double r_E = L[nc + cc] * (s * (double)v[nc + cc]);
-    double r_e = (r_E - E * r_rho) / rho;
-    double e = E;
+    const T s = vslot >= 0 ? (T)vscale[vslot] : (T)1;
+    T r_rho = C[PcLr * nc + cc] * (s * v[cc]);
+    T r_E = C[PcLE * nc + cc] * (s * v[nc + cc]);
+    T r_e = (r_E - C[PcE * nc + cc] * r_rho) * C[PcInvRho * nc + cc];
+    T ruv[ND];
+    T dot_ur = (T)0;
+#pragma unroll
+    for (int c = 0; c < ND; ++c) ruv[c] = ru_at<T, T>(G, C, v, s, c, P);
     if (G.energy_form == 1) {
-        double dot = 0.0, ke = 0.0;
-        for (int d = 0; d < G.ndim; ++d) {
-            const double* ud = X + (2 + d) * nc;
-            int o[3] = {0, 0, 0};
-            o[d] = 1;
-            double ul = load_normal(G, ud, d, P, 0, 0, 0);
-            double uu = load_normal(G, ud, d, P, o[0], o[1], o[2]);
-            double al = ru_face(G, X, L, v, s, d, P, false);
-            double au = ru_face(G, X, L, v, s, d, P, true);
-            dot = dot + 0.5 * (ul * al + uu * au);
-            ke = ke + 0.25 * (ul * ul + uu * uu);
+        T dot = (T)0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            Idx3 Q = P;
+            T uu = (T)0, au = (T)0;
+            if (!(G.bc[d] == 1 && P.i[d] + 1 == G.n[d])) {
+                Q.i[d] = (P.i[d] + 1 == G.n[d]) ? 0 : P.i[d] + 1;
+                uu = C[(PcU + d) * nc + flat(G, Q.i[0], Q.i[1], Q.i[2])];
+                au = ru_at<T, T>(G, C, v, s, d, Q);
+            }
+            dot = dot + (T)0.5 * (C[(PcU + d) * nc + cc] * ruv[d] + uu * au);
         }
         r_e = r_e - dot;
-        e = E - ke;
+        dot_ur = dot;
     }
-    for (int c = 0; c < G.ndim; ++c) ru[c * nc + cc] = (T)ru_face(G, X, L, v, s, c, P, false);
-    double dpdrho = G.gm1 * e;
-    double dpde = G.gm1 * rho;
-    double r_p = dpdrho * r_rho + dpde * r_e;
-    rp[cc] = (T)r_p;
-    re[cc] = (T)r_e;
-    double p = G.gm1 * rho * e;
-    Binv2 B = si_B(G, rho, p, dt, nf);
-    if (nf == 1) {
-        rhs[cc] = (T)(r_p / B.bpp);
-        x0[cc] = (T)0;
+#pragma unroll
+    for (int c = 0; c < ND; ++c) ru[c * nc + cc] = ruv[c];
+    re[cc] = r_e;
+    if (sizeof(T) == 8) {
+        // double: the oracle's order, r_p = dp/drho r_rho + dp/de r_e, rhs = B^-1 (r_p, r_e)
+        T r_p = C[PcDpdrho * nc + cc] * r_rho + C[PcDpde * nc + cc] * r_e;
+        rp[cc] = r_p;
+        if (nf == 1) {
+            rhs[cc] = r_p * C[PcQ0 * nc + cc];
+        } else {
+            rhs[cc] = C[PcQ0 * nc + cc] * r_p + C[PcQ1 * nc + cc] * r_e;
+            rhs[nc + cc] = C[PcQ2 * nc + cc] * r_p + C[PcQ3 * nc + cc] * r_e;
+        }
     } else {
-        rhs[cc] = (T)(B.b00 * r_p + B.b01 * r_e);
-        rhs[nc + cc] = (T)(B.b10 * r_p + B.b11 * r_e);
-        x0[cc] = (T)0;
-        x0[nc + cc] = (T)0;
+        // float: folded coefficients (see PcQ*), free of cancellation
+        T r_p = C[PcPr * nc + cc] * r_rho + C[PcPE * nc + cc] * r_E - C[PcDpde * nc + cc] * dot_ur;
+        rp[cc] = r_p;
+        rhs[cc] = C[PcQ0 * nc + cc] * r_rho + C[PcQ1 * nc + cc] * r_E - C[PcQ2 * nc + cc] * dot_ur;
+        if (nf == 2)
+            rhs[nc + cc] = C[PcQ3 * nc + cc] * r_rho + C[PcQ4 * nc + cc] * r_E - C[PcQ5 * nc + cc] * dot_ur;
     }
+    x0[cc] = (T)0;
+    if (nf == 2) x0[nc + cc] = (T)0;
 }
 
-template <typename TV, typename T>
-void launch_precond_in(const Grid& G, const double* X, const double* L, const TV* v, const double* vscale, int vslot,
-                       double dt, int nf, T* rp, T* re, T* ru, MGLevel& L0, cudaStream_t s) {
-    ++g_launch_count;
-    k_precond_in<TV, T><<<nb(G.ncell), kBlock, 0, s>>>(G, X, L, v, vscale, vslot, dt, nf, rp, re, ru, (T*)L0.rhs,
-                                                      (T*)L0.x);
+template <typename T>
+void launch_precond_in(const Grid& G, const T* C, const T* v, const double* vscale, int vslot, int nf, T* rp, T* re,
+                       T* ru, MGLevel& L0, cudaStream_t s) {
+    CELL_LAUNCH_T(k_precond_in, T, G, C, v, vscale, vslot, nf, rp, re, ru, (T*)L0.rhs, (T*)L0.x);
 }
-template void launch_precond_in<double, double>(const Grid&, const double*, const double*, const double*,
-                                                const double*, int, double, int, double*, double*, double*, MGLevel&,
-                                                cudaStream_t);
-template void launch_precond_in<float, float>(const Grid&, const double*, const double*, const float*, const double*,
-                                              int, double, int, float*, float*, float*, MGLevel&, cudaStream_t);
+template void launch_precond_in<double>(const Grid&, const double*, const double*, const double*, int, int, double*,
+                                        double*, double*, MGLevel&, cudaStream_t);
+template void launch_precond_in<float>(const Grid&, const float*, const float*, const double*, int, int, float*,
+                                       float*, float*, MGLevel&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // multigrid
 // ---------------------------------------------------------------------------
 
+// Red-black Gauss-Seidel half sweep over the cells of one colour (parity of
+// i+j+k).  With an even x extent each thread takes one cell of the colour
+// (compact mapping); otherwise threads of the other colour return.
 template <typename T, int NF>
 __global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
-                         const T* __restrict__ rhs, int colour) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= Lv.nc) return;
+                         const T* __restrict__ rhs, int colour, int compact) {
     int i[3];
-    i[0] = (int)(cc % Lv.n[0]);
-    long long t = cc / Lv.n[0];
-    i[1] = (int)(t % Lv.n[1]);
-    i[2] = (int)(t / Lv.n[1]);
+    i[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    i[2] = blockIdx.z;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (compact) i[0] = 2 * t + ((i[1] + i[2] + colour) & 1);
+    else i[0] = t;
+    if (i[0] >= Lv.n[0] || i[1] >= Lv.n[1]) return;
     if (((i[0] + i[1] + i[2]) & 1) != colour) return;
+    const long long cc = lflat(Lv, i[0], i[1], i[2]);
     T dg[NF], of[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -340,7 +410,7 @@ __global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* 
             long long ju = lflat(Lv, up[0], up[1], up[2]), jd = lflat(Lv, dn[0], dn[1], dn[2]);
             const T* Kd = K + (f * ndim + d) * Lv.nc;
             T Kl = Kd[cc], Ku = Kd[ju];
-            T ih2 = (T)Lv.ih2[d];
+            T ih2 = ih2_of<T>(Lv, d);
             dg[f] = dg[f] + (Kl + Ku) * ih2;
             of[f] = of[f] + (Ku * xf[ju] + Kl * xf[jd]) * ih2;
         }
@@ -358,13 +428,16 @@ __global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* 
 
 template <typename T>
 void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s) {
+    int compact = (Lv.n[0] % 2 == 0) ? 1 : 0;
+    int nx[3] = {compact ? Lv.n[0] / 2 : Lv.n[0], Lv.n[1], Lv.n[2]};
+    CellLaunch cl = cell_launch(nx);
     ++g_launch_count;
     if (nf == 1)
-        k_smooth<T, 1><<<nb(Lv.ncell), kBlock, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
-                                                       (const T*)Lv.rhs, colour);
+        k_smooth<T, 1><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
+                                                    (const T*)Lv.rhs, colour, compact);
     else
-        k_smooth<T, 2><<<nb(Lv.ncell), kBlock, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
-                                                       (const T*)Lv.rhs, colour);
+        k_smooth<T, 2><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
+                                                    (const T*)Lv.rhs, colour, compact);
 }
 template void launch_smooth<double>(const Grid&, int, MGLevel&, int, cudaStream_t);
 template void launch_smooth<float>(const Grid&, int, MGLevel&, int, cudaStream_t);
@@ -387,7 +460,7 @@ __device__ __forceinline__ T fine_residual(int ndim, const LvlDev& F, const T* M
         long long ju = lflat(F, up[0], up[1], up[2]), jd = lflat(F, dn[0], dn[1], dn[2]);
         const T* Kd = K + (f * ndim + d) * F.nc;
         T Kl = Kd[cc], Ku = Kd[ju];
-        out = out - (Ku * (xf[ju] - xf[cc]) - Kl * (xf[cc] - xf[jd])) * (T)F.ih2[d];
+        out = out - (Ku * (xf[ju] - xf[cc]) - Kl * (xf[cc] - xf[jd])) * ih2_of<T>(F, d);
     }
     return rhs[f * F.nc + cc] - out;
 }
@@ -396,12 +469,10 @@ template <typename T, int NF>
 __global__ void k_restrict(int ndim, LvlDev F, LvlDev C, const T* __restrict__ M, const T* __restrict__ K,
                            const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ rhsc,
                            T* __restrict__ xc) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= C.nc) return;
-    int a = (int)(cc % C.n[0]);
-    long long t = cc / C.n[0];
-    int b = (int)(t % C.n[1]);
-    int c = (int)(t / C.n[1]);
+    int ic[3];
+    long long cc;
+    if (!lvl_pos(C, ic, cc)) return;
+    const int a = ic[0], b = ic[1], c = ic[2];
     int cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
     int nx = cd[0] ? 2 : 1, ny = cd[1] ? 2 : 1, nz = cd[2] ? 2 : 1;
     int x0 = cd[0] ? 2 * a : a, y0 = cd[1] ? 2 * b : b, z0 = cd[2] ? 2 * c : c;
@@ -424,13 +495,14 @@ __global__ void k_restrict(int ndim, LvlDev F, LvlDev C, const T* __restrict__ M
 
 template <typename T>
 void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
+    CellLaunch cl = cell_launch(C.n);
     ++g_launch_count;
     if (nf == 1)
-        k_restrict<T, 1><<<nb(C.ncell), kBlock, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
-                                                       (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
+        k_restrict<T, 1><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
+                                                      (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
     else
-        k_restrict<T, 2><<<nb(C.ncell), kBlock, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
-                                                       (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
+        k_restrict<T, 2><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
+                                                      (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
 }
 template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
 template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
@@ -446,13 +518,9 @@ __device__ __forceinline__ void parents(int i, int nc, int bc, int& par, int& ot
 template <typename T, int NF>
 __global__ void k_prolong(int ndim, int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
                           T* __restrict__ xf) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= F.nc) return;
     int i[3];
-    i[0] = (int)(cc % F.n[0]);
-    long long t = cc / F.n[0];
-    i[1] = (int)(t % F.n[1]);
-    i[2] = (int)(t / F.n[1]);
+    long long cc;
+    if (!lvl_pos(F, i, cc)) return;
     int bc[3] = {bc0, bc1, bc2};
     int pa[3], ot[3], cd[3];
     for (int d = 0; d < 3; ++d) {
@@ -483,13 +551,14 @@ __global__ void k_prolong(int ndim, int bc0, int bc1, int bc2, LvlDev F, LvlDev 
 
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
+    CellLaunch cl = cell_launch(F.n);
     ++g_launch_count;
     if (nf == 1)
-        k_prolong<T, 1><<<nb(F.ncell), kBlock, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
-                                                      (const T*)C.x, (T*)F.x);
+        k_prolong<T, 1><<<cl.grid, cl.block, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
+                                                     (const T*)C.x, (T*)F.x);
     else
-        k_prolong<T, 2><<<nb(F.ncell), kBlock, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
-                                                      (const T*)C.x, (T*)F.x);
+        k_prolong<T, 2><<<cl.grid, cl.block, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
+                                                     (const T*)C.x, (T*)F.x);
 }
 template void launch_prolong<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
 template void launch_prolong<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
@@ -519,15 +588,10 @@ template void launch_coarsest<float>(int, MGLevel&, cudaStream_t);
 // back substitution and transform out
 // ---------------------------------------------------------------------------
 
+// du on the lower face of cell Q in direction c
 template <typename T>
-__device__ __forceinline__ double du_face(const Grid& G, const double* X, double dt, const T* ru, const T* dp, int c,
-                                          const Idx3& P, bool up) {
-    Idx3 Q = P;
-    if (up) {
-        if (G.bc[c] == 1 && P.i[c] + 1 == G.n[c]) return 0.0;
-        Q.i[c] = (P.i[c] + 1 == G.n[c]) ? 0 : P.i[c] + 1;
-    }
-    if (is_wall_slot(G, c, Q)) return 0.0;
+__device__ __forceinline__ T du_at(const Grid& G, const T* C, T dt, const T* ru, const T* dp, int c, const Idx3& Q) {
+    const long long nc = G.ncell;
     const long long j = flat(G, Q.i[0], Q.i[1], Q.i[2]);
     int o[3] = {0, 0, 0};
     o[c] = -1;
@@ -535,75 +599,68 @@ __device__ __forceinline__ double du_face(const Grid& G, const double* X, double
     int b = cell_map(Q.i[1] + o[1], G.n[1], G.bc[1]);
     int cz = cell_map(Q.i[2] + o[2], G.n[2], G.bc[2]);
     long long jl = flat(G, a, b, cz);
-    double gp = ((double)dp[j] - (double)dp[jl]) * G.idx[c];
-    double rho_f = 0.5 * (X[jl] + X[j]);
-    return dt * ((double)ru[c * G.ncell + j] - G.theta * gp / rho_f);
+    return dt * (ru[c * nc + j] - C[(PcThf + c) * nc + j] * (dp[j] - dp[jl]));
 }
 
-template <typename T, typename TO>
-__global__ void k_precond_out(Grid G, const double* __restrict__ X, const double* __restrict__ Rinv, double dt, int nf,
-                              const T* __restrict__ rp, const T* __restrict__ re, const T* __restrict__ ru,
-                              const T* __restrict__ x, TO* __restrict__ z, double* __restrict__ partials) {
+template <int ND, typename T>
+__global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int nf, const T* __restrict__ rp,
+                              const T* __restrict__ re, const T* __restrict__ ru, const T* __restrict__ x,
+                              T* __restrict__ z, double* __restrict__ partials) {
     __shared__ double sh[32];
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    Idx3 P;
+    long long cc;
     double acc = 0.0;
-    if (cc < G.ncell) {
+    if (cell_pos(G.n, P, cc)) {
         const long long nc = G.ncell;
-        Idx3 P = decompose(G, cc);
-        double rho = X[cc];
-        double E = X[nc + cc];
-        double e = E;
-        double dp = (double)x[cc];
-        double de;
-        if (nf == 1) de = dt * ((double)re[cc] + (dp / dt - (double)rp[cc]) / (G.gamma * rho));
-        else de = (double)x[nc + cc];
-        double dE = de;
+        const T dt = (T)dt_d;
+        const T dp = x[cc];
+        T de;
+        if (nf == 1) de = dt * (re[cc] + (dp * (T)(1.0 / dt_d) - rp[cc]) * C[PcCde * nc + cc]);
+        else de = x[nc + cc];
+        T du[ND];
+#pragma unroll
+        for (int c = 0; c < ND; ++c) du[c] = du_at<T>(G, C, dt, ru, x, c, P);
+        T dE = de;
         if (G.energy_form == 1) {
-            double dot = 0.0, ke = 0.0;
-            for (int d = 0; d < G.ndim; ++d) {
-                const double* ud = X + (2 + d) * nc;
-                int o[3] = {0, 0, 0};
-                o[d] = 1;
-                double ul = load_normal(G, ud, d, P, 0, 0, 0);
-                double uu = load_normal(G, ud, d, P, o[0], o[1], o[2]);
-                double al = du_face<T>(G, X, dt, ru, x, d, P, false);
-                double au = du_face<T>(G, X, dt, ru, x, d, P, true);
-                dot = dot + 0.5 * (ul * al + uu * au);
-                ke = ke + 0.25 * (ul * ul + uu * uu);
+            T dot = (T)0;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                T uu = (T)0, au = (T)0;
+                if (!(G.bc[d] == 1 && P.i[d] + 1 == G.n[d])) {
+                    Idx3 Q = P;
+                    Q.i[d] = (P.i[d] + 1 == G.n[d]) ? 0 : P.i[d] + 1;
+                    uu = C[(PcU + d) * nc + flat(G, Q.i[0], Q.i[1], Q.i[2])];
+                    au = du_at<T>(G, C, dt, ru, x, d, Q);
+                }
+                dot = dot + (T)0.5 * (C[(PcU + d) * nc + cc] * du[d] + uu * au);
             }
             dE = de + dot;
-            e = E - ke;
         }
-        double dpdrho = G.gm1 * e;
-        double dpde = G.gm1 * rho;
-        double drho = (dp - dpde * de) / dpdrho;
-        double out[5];
-        out[0] = drho;
-        out[1] = dE;
-        for (int c = 0; c < G.ndim; ++c) out[2 + c] = du_face<T>(G, X, dt, ru, x, c, P, false);
-        for (int k = 0; k < 2 + G.ndim; ++k) {
-            long long j = k * nc + cc;
-            TO zv = (TO)(out[k] * Rinv[j]);
-            z[j] = zv;
-            double zd = (double)zv;
+        T drho = (dp - C[PcDpde * nc + cc] * de) * C[PcInvDpdrho * nc + cc];
+        T out[2 + ND];
+        out[0] = drho * C[PcRinvR * nc + cc];
+        out[1] = dE * C[PcRinvE * nc + cc];
+#pragma unroll
+        for (int c = 0; c < ND; ++c) out[2 + c] = du[c] * C[(PcRinvU + c) * nc + cc];
+#pragma unroll
+        for (int k = 0; k < 2 + ND; ++k) {
+            z[k * nc + cc] = out[k];
+            double zd = (double)out[k];
             acc += zd * zd;
         }
     }
-    double s = block_sum<kBlock>(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    double s = block_sum<128>(acc, sh);
+    if (thread_linear() == 0) partials[block_linear()] = s;
 }
 
-template <typename T, typename TO>
-void launch_precond_out(const Grid& G, const double* X, const double* Rinv, double dt, int nf, const T* rp,
-                        const T* re, const T* ru, const MGLevel& L0, TO* z, double* partials, cudaStream_t s) {
-    ++g_launch_count;
-    k_precond_out<T, TO><<<nb(G.ncell), kBlock, 0, s>>>(G, X, Rinv, dt, nf, rp, re, ru, (const T*)L0.x, z, partials);
+template <typename T>
+void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
+                        const MGLevel& L0, T* z, double* partials, cudaStream_t s) {
+    CELL_LAUNCH_T(k_precond_out, T, G, C, dt, nf, rp, re, ru, (const T*)L0.x, z, partials);
 }
-template void launch_precond_out<double, double>(const Grid&, const double*, const double*, double, int, const double*,
-                                                 const double*, const double*, const MGLevel&, double*, double*,
-                                                 cudaStream_t);
-template void launch_precond_out<float, float>(const Grid&, const double*, const double*, double, int, const float*,
-                                               const float*, const float*, const MGLevel&, float*, double*,
-                                               cudaStream_t);
+template void launch_precond_out<double>(const Grid&, const double*, double, int, const double*, const double*,
+                                         const double*, const MGLevel&, double*, double*, cudaStream_t);
+template void launch_precond_out<float>(const Grid&, const float*, double, int, const float*, const float*,
+                                        const float*, const MGLevel&, float*, double*, cudaStream_t);
 
 }  // namespace jfnk

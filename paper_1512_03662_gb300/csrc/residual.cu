@@ -35,16 +35,18 @@ __global__ void k_perturb(Grid G, const double* __restrict__ X, const TZ* __rest
     Xp[k] = X[k] + delta * (R[k] * (double)z[k]);
 }
 
+template <int ND>
 __global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__ p, double* __restrict__ T) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= G.ncell) return;
+    Idx3 P;
+    long long c;
+    if (!cell_pos(G.n, P, c)) return;
     const long long nc = G.ncell;
     double rho = X[c];
     double e = X[nc + c];
     if (G.energy_form == 1) {
-        Idx3 P = decompose(G, c);
         double ke = 0.0;
-        for (int d = 0; d < G.ndim; ++d) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
             const double* u = X + (2 + d) * nc;
             int o[3] = {0, 0, 0};
             o[d] = 1;
@@ -62,35 +64,27 @@ __device__ __forceinline__ double conductivity(const Grid& G, double T) {
     return G.chi_exp == 3.0 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
 }
 
+template <int ND>
 __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ p,
-                              const double* __restrict__ T, double* __restrict__ Fm, double* __restrict__ FE) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= G.ncell) return;
+                              const double* __restrict__ T, double* __restrict__ Fmh, double* __restrict__ FE) {
+    Idx3 P;
+    long long c;
+    if (!cell_pos(G.n, P, c)) return;
     const long long nc = G.ncell;
-    Idx3 P = decompose(G, c);
     const double* rho = X;
     const double* E = X + nc;
-    for (int d = 0; d < G.ndim; ++d) {
+    const double r0 = __ldg(rho + c), e0 = __ldg(E + c);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
         int o[3] = {0, 0, 0};
         const double u = load_normal(G, X + (2 + d) * nc, d, P, 0, 0, 0);
-        double rho_up, E_up;
-        if (u >= 0.0) {
-            o[d] = -2; double r2 = load_cell(G, rho, P, o[0], o[1], o[2]); double e2 = load_cell(G, E, P, o[0], o[1], o[2]);
-            o[d] = -1; double r1 = load_cell(G, rho, P, o[0], o[1], o[2]); double e1 = load_cell(G, E, P, o[0], o[1], o[2]);
-            double r0 = __ldg(rho + c), e0 = __ldg(E + c);
-            double sr = vanleer(r1 - r2, r0 - r1);
-            double se = vanleer(e1 - e2, e0 - e1);
-            rho_up = r1 + 0.5 * sr;
-            E_up = e1 + 0.5 * se;
-        } else {
-            o[d] = -1; double r1 = load_cell(G, rho, P, o[0], o[1], o[2]); double e1 = load_cell(G, E, P, o[0], o[1], o[2]);
-            o[d] = 1;  double r3 = load_cell(G, rho, P, o[0], o[1], o[2]); double e3 = load_cell(G, E, P, o[0], o[1], o[2]);
-            double r0 = __ldg(rho + c), e0 = __ldg(E + c);
-            double sr = vanleer(r0 - r1, r3 - r0);
-            double se = vanleer(e0 - e1, e3 - e0);
-            rho_up = r0 - 0.5 * sr;
-            E_up = e0 - 0.5 * se;
-        }
+        o[d] = -2; const double r2 = load_cell(G, rho, P, o[0], o[1], o[2]), e2 = load_cell(G, E, P, o[0], o[1], o[2]);
+        o[d] = -1; const double r1 = load_cell(G, rho, P, o[0], o[1], o[2]), e1 = load_cell(G, E, P, o[0], o[1], o[2]);
+        o[d] = 1;  const double r3 = load_cell(G, rho, P, o[0], o[1], o[2]), e3 = load_cell(G, E, P, o[0], o[1], o[2]);
+        // upwind side: cell i-1 for u >= 0 (ties to the lower side), else cell i
+        const bool left = u >= 0.0;
+        const double rho_up = upwind_value(left ? r1 : r0, left ? r2 : r3, left ? r0 : r1);
+        const double E_up = upwind_value(left ? e1 : e0, left ? e2 : e3, left ? e0 : e1);
         double fm = u * rho_up;
         double fe = fm * E_up;
         o[d] = -1;
@@ -104,7 +98,7 @@ __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double
             double q = 0.5 * (conductivity(G, Tl) + conductivity(G, Tc)) * (Tc - Tl) * G.idx[d];
             fe = fe - q;
         }
-        Fm[d * nc + c] = fm;
+        Fmh[d * nc + c] = 0.5 * fm;           // half mass flux: every consumer averages two of them
         FE[d * nc + c] = fe;
     }
 }
@@ -123,82 +117,76 @@ __device__ __forceinline__ double load_face_up(const Grid& G, const double* f, i
     return load_cell(G, f, P, o[0], o[1], o[2]);
 }
 
-__global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ Fm,
+template <int ND>
+__global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ Fmh,
                              double* __restrict__ Psi) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= G.ncell) return;
+    Idx3 P;
+    long long cc;
+    if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
-    Idx3 P = decompose(G, cc);
-    const int nd = G.ndim;
+    constexpr int nd = ND;
+#pragma unroll
     for (int c = 0; c < nd; ++c) {
         const double* uc = X + (2 + c) * nc;
+#pragma unroll
         for (int d = 0; d < nd; ++d) {
-            double psi;
+            double m, q_near, q_far, q_other;
+            int o[3] = {0, 0, 0};
             if (c == d) {
-                // flux at the cell centre between faces i and i+1 along c
-                double m = 0.5 * (__ldg(Fm + c * nc + cc) + load_face_up(G, Fm + c * nc, c, P));
-                int o[3] = {0, 0, 0};
-                double uup;
-                if (m >= 0.0) {
-                    o[c] = -1; double um = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
-                    o[c] = 1;  double up = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    uup = u0 + 0.5 * vanleer(u0 - um, up - u0);
-                } else {
-                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
-                    o[c] = 1;  double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    o[c] = 2;  double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    uup = u1 - 0.5 * vanleer(u1 - u0, u2 - u1);
-                }
-                psi = m * uup;
+                // flux at the cell centre between faces i and i+1 along c, carried
+                // by the mean of the two mass fluxes (stored halved)
+                m = __ldg(Fmh + c * nc + cc) + load_face_up(G, Fmh + c * nc, c, P);
+                o[c] = -1; const double um = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
+                o[c] = 1;  const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                o[c] = 2;  const double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                const bool left = m >= 0.0;
+                q_near = left ? u0 : u1;
+                q_far = left ? um : u2;
+                q_other = left ? u1 : u0;
             } else {
                 // flux on the edge between c-face i_c and d-face i_d
-                int o[3] = {0, 0, 0};
                 o[c] = -1;
-                double m = 0.5 * (load_Fm_cell(G, Fm + d * nc, P, o[0], o[1], o[2]) + __ldg(Fm + d * nc + cc));
+                m = load_Fm_cell(G, Fmh + d * nc, P, o[0], o[1], o[2]) + __ldg(Fmh + d * nc + cc);
                 o[c] = 0;
-                double uup;
-                if (m >= 0.0) {
-                    o[d] = -2; double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    o[d] = -1; double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
-                    uup = u1 + 0.5 * vanleer(u1 - u2, u0 - u1);
-                } else {
-                    o[d] = -1; double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    double u0 = load_normal(G, uc, c, P, 0, 0, 0);
-                    o[d] = 1;  double u3 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                    uup = u0 - 0.5 * vanleer(u0 - u1, u3 - u0);
-                }
-                psi = m * uup;
+                o[d] = -2; const double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                o[d] = -1; const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
+                o[d] = 1;  const double u3 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
+                const bool left = m >= 0.0;
+                q_near = left ? u1 : u0;
+                q_far = left ? u2 : u3;
+                q_other = left ? u0 : u1;
             }
-            Psi[(c * nd + d) * nc + cc] = psi;
+            Psi[(c * nd + d) * nc + cc] = m * upwind_value(q_near, q_far, q_other);
         }
     }
 }
 
-template <int MODE, typename TO>
+template <int ND, int MODE, typename TO>
 __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* __restrict__ p,
                            const double* __restrict__ Fm, const double* __restrict__ FE,
                            const double* __restrict__ Psi, const double* __restrict__ bn,
                            const double* __restrict__ G0, const double* __restrict__ Linv,
                            const double* __restrict__ scal, int delta_slot, double dt_inv,
                            double* __restrict__ outd, TO* __restrict__ outb) {
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cc >= G.ncell) return;
+    Idx3 P;
+    long long cc;
+    if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
-    const int nd = G.ndim;
-    Idx3 P = decompose(G, cc);
+    constexpr int nd = ND;
     const double th = G.theta;
     double inv_delta = 0.0;
     if (MODE == kModeJv) inv_delta = 1.0 / scal[delta_slot];
 
     double Rr = 0.0, RE = 0.0, divu = 0.0;
+#pragma unroll
     for (int d = 0; d < nd; ++d) {
         const double* fmd = Fm + d * nc;
         const double* fed = FE + d * nc;
         double fm0 = __ldg(fmd + cc), fm1 = load_face_up(G, fmd, d, P);
         double fe0 = __ldg(fed + cc), fe1 = load_face_up(G, fed, d, P);
-        Rr = Rr - (fm1 - fm0) * G.idx[d];
+        Rr = Rr - (fm1 - fm0) * G.tidx[d];                  // Fm stored halved
         RE = RE - (fe1 - fe0) * G.idx[d];
         if (G.energy_form == 0) {
             const double* ud = X + (2 + d) * nc;
@@ -208,16 +196,17 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
             double u1 = load_normal(G, ud, d, P, o[0], o[1], o[2]);
             divu = divu + (u1 - u0) * G.idx[d];
         } else if (G.g[d] != 0.0) {
-            RE = RE + G.g[d] * 0.5 * (fm0 + fm1);
+            RE = RE + G.g[d] * (fm0 + fm1);
         }
     }
     const double pc = __ldg(p + cc);
     if (G.energy_form == 0) RE = RE - pc * divu;
 
     const double rho = __ldg(X + cc);
-    double Uv[5], Rv[5];
+    double Uv[2 + ND], Rv[2 + ND];
     Uv[0] = rho;            Rv[0] = Rr;
     Uv[1] = rho * __ldg(X + nc + cc); Rv[1] = RE;
+#pragma unroll
     for (int c = 0; c < nd; ++c) {
         if (is_wall_slot(G, c, P)) { Uv[2 + c] = 0.0; Rv[2 + c] = 0.0; continue; }
         int o[3] = {0, 0, 0};
@@ -227,6 +216,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         double rho_f = 0.5 * (rl + rho);
         double Rc = -(pc - pl) * G.idx[c];
         if (G.g[c] != 0.0) Rc = Rc + rho_f * G.g[c];
+#pragma unroll
         for (int d = 0; d < nd; ++d) {
             const double* ps = Psi + (c * nd + d) * nc;
             double a, b;
@@ -243,6 +233,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         Uv[2 + c] = rho_f * __ldg(X + (2 + c) * nc + cc);
         Rv[2 + c] = Rc;
     }
+#pragma unroll
     for (int k = 0; k < 2 + nd; ++k) {
         const long long j = k * nc + cc;
         const bool wall = (k >= 2) && is_wall_slot(G, k - 2, P);
@@ -287,22 +278,23 @@ __device__ __forceinline__ double internal_e(const Grid& G, const double* X, con
     return E - ke;
 }
 
+template <int ND>
 __global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, double alpha2,
                           double* __restrict__ L, double* __restrict__ R, double* __restrict__ Linv,
                           double* __restrict__ Rinv, double* __restrict__ partials) {
     __shared__ double sh[32];
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    Idx3 P;
+    long long cc;
     double acc = 0.0;
-    if (cc < G.ncell) {
+    if (cell_pos(G.n, P, cc)) {
         const long long nc = G.ncell;
-        Idx3 P = decompose(G, cc);
         double rho = X[cc], E = X[nc + cc];
         double Lv[5], Rv[5];
         Lv[0] = rho; Rv[0] = rho;
         Lv[1] = rho * E; Rv[1] = E;
         double e0 = internal_e(G, X, P, 0, 0, 0);
         double cs0 = sqrt(G.gamma * G.gm1 * e0);
-        for (int c = 0; c < G.ndim; ++c) {
+        for (int c = 0; c < ND; ++c) {
             if (is_wall_slot(G, c, P)) { Lv[2 + c] = 1.0; Rv[2 + c] = 1.0; continue; }
             int o[3] = {0, 0, 0};
             o[c] = -1;
@@ -315,7 +307,7 @@ __global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, d
             Lv[2 + c] = rho_f * fmax(au, alpha1 * cs_f);
             Rv[2 + c] = fmax(au, alpha2 * cs_f);
         }
-        for (int k = 0; k < 2 + G.ndim; ++k) {
+        for (int k = 0; k < 2 + ND; ++k) {
             long long j = k * nc + cc;
             L[j] = Lv[k];
             R[j] = Rv[k];
@@ -326,20 +318,21 @@ __global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, d
             acc += xh * xh;
         }
     }
-    double s = block_sum<kBlock>(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    double s = block_sum<128>(acc, sh);
+    if (thread_linear() == 0) partials[block_linear()] = s;
 }
 
 // max over cells of |u_cell| + c_s (Sect. 1, CFL_hydro)
+template <int ND>
 __global__ void k_signal_speed(Grid G, const double* __restrict__ X, double* __restrict__ partials) {
     __shared__ double sh[32];
-    long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    Idx3 P;
+    long long cc;
     double v = 0.0;
-    if (cc < G.ncell) {
+    if (cell_pos(G.n, P, cc)) {
         const long long nc = G.ncell;
-        Idx3 P = decompose(G, cc);
         double s = 0.0;
-        for (int c = 0; c < G.ndim; ++c) {
+        for (int c = 0; c < ND; ++c) {
             int o[3] = {0, 0, 0};
             o[c] = 1;
             double u0 = load_normal(G, X + (2 + c) * nc, c, P, 0, 0, 0);
@@ -351,8 +344,8 @@ __global__ void k_signal_speed(Grid G, const double* __restrict__ X, double* __r
         v = sqrt(s) + sqrt(G.gamma * G.gm1 * e);
         if (!(v == v)) v = __longlong_as_double(0x7ff8000000000000ULL);
     }
-    double m = block_max<kBlock>(v, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+    double m = block_max<128>(v, sh);
+    if (thread_linear() == 0) partials[block_linear()] = m;
 }
 
 // --------------------------------------------------------------------------
@@ -361,9 +354,16 @@ __global__ void k_signal_speed(Grid G, const double* __restrict__ X, double* __r
 
 static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+#define CELL_LAUNCH(KERNEL, ...)                                                          \
+    do {                                                                                  \
+        CellLaunch cl_ = cell_launch(G.n);                                                \
+        ++g_launch_count;                                                                 \
+        if (G.ndim == 3) KERNEL<3><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);           \
+        else KERNEL<2><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);                       \
+    } while (0)
+
 void launch_eos(const Grid& G, const double* X, double* p, double* T, cudaStream_t s) {
-    ++g_launch_count;
-    k_eos<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, p, T);
+    CELL_LAUNCH(k_eos, G, X, p, T);
 }
 
 template <typename TZ>
@@ -380,13 +380,11 @@ template void launch_perturb<float>(const Grid&, const double*, const float*, co
 
 void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
                         cudaStream_t s) {
-    ++g_launch_count;
-    k_face_fluxes<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, p, T, Fm, FE);
+    CELL_LAUNCH(k_face_fluxes, G, X, p, T, Fm, FE);
 }
 
 void launch_mom_fluxes(const Grid& G, const double* X, const double* Fm, double* Psi, cudaStream_t s) {
-    ++g_launch_count;
-    k_mom_fluxes<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, Fm, Psi);
+    CELL_LAUNCH(k_mom_fluxes, G, X, Fm, Psi);
 }
 
 void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
@@ -399,9 +397,14 @@ template <int MODE, typename TO>
 void launch_assemble(const Grid& G, const double* X, const double* p, const double* Fm, const double* FE,
                      const double* Psi, const double* bn, const double* G0, const double* Linv, const double* scal,
                      int slot, double dt, double* outd, TO* outb, cudaStream_t s) {
+    CellLaunch cl = cell_launch(G.n);
     ++g_launch_count;
-    k_assemble<MODE, TO><<<nblk(G.ncell), kBlock, 0, s>>>(G, X, p, Fm, FE, Psi, bn, G0, Linv, scal, slot, 1.0 / dt,
-                                                         outd, outb);
+    if (G.ndim == 3)
+        k_assemble<3, MODE, TO><<<cl.grid, cl.block, 0, s>>>(G, X, p, Fm, FE, Psi, bn, G0, Linv, scal, slot, 1.0 / dt,
+                                                           outd, outb);
+    else
+        k_assemble<2, MODE, TO><<<cl.grid, cl.block, 0, s>>>(G, X, p, Fm, FE, Psi, bn, G0, Linv, scal, slot, 1.0 / dt,
+                                                           outd, outb);
 }
 #define INST(M, T)                                                                                             \
     template void launch_assemble<M, T>(const Grid&, const double*, const double*, const double*, const double*, \
@@ -418,15 +421,16 @@ INST(kModeJv, float)
 
 void launch_scaling(const Grid& G, const double* X, double a1, double a2, double* L, double* R, double* Linv,
                     double* Rinv, double* partials, cudaStream_t s) {
-    ++g_launch_count;
-    k_scaling<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, a1, a2, L, R, Linv, Rinv, partials);
+    CELL_LAUNCH(k_scaling, G, X, a1, a2, L, R, Linv, Rinv, partials);
 }
 
 void launch_signal_speed(const Grid& G, const double* X, double* partials, cudaStream_t s) {
-    ++g_launch_count;
-    k_signal_speed<<<nblk(G.ncell), kBlock, 0, s>>>(G, X, partials);
+    CELL_LAUNCH(k_signal_speed, G, X, partials);
 }
 
-unsigned cell_blocks(const Grid& G) { return nblk(G.ncell); }
+unsigned cell_blocks(const Grid& G) {
+    CellLaunch cl = cell_launch(G.n);
+    return cl.grid.x * cl.grid.y * cl.grid.z;
+}
 
 }  // namespace jfnk
