@@ -185,6 +185,24 @@ jfnk_status jfnk_dt_from_cfl(jfnk_handle* h, const double* X, double cfl, double
  * accounting: enable with on = 1 (CUDA events on the bound stream). */
 jfnk_status jfnk_set_profiling(jfnk_handle* h, int on);
 
+/* Largest grid (cells) that jfnk_residual_noalloc accepts. */
+#define JFNK_NOALLOC_MAX_CELLS 65536
+
+/* The residual of jfnk_residual, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is an interface variant.
+ * Same arguments, layout and result as jfnk_residual, but the scratch it needs
+ * (b^n, p, T and the flux fields) lives in a fixed array inside the library
+ * (JFNK_NOALLOC_MAX_CELLS * 22 doubles, 11.5 MB, held on every GPU that loads
+ * the library until the process exits) instead of the bound workspace, so
+ * the handle needs no jfnk_bind and the call allocates nothing.  Grids above
+ * JFNK_NOALLOC_MAX_CELLS cells return JFNK_EINVAL with a message.  The first
+ * call made with a given device current looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU race, so
+ * serialise them.  Queued on the handle's stream (the legacy default stream
+ * if the handle was never bound). */
+jfnk_status jfnk_residual_noalloc(jfnk_handle* h, const double* X, const double* Xn, double dt, double* F);
+
 /* Message of the last error on this handle (never NULL). */
 const char* jfnk_last_error(const jfnk_handle* h);
 

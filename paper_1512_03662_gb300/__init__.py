@@ -108,6 +108,7 @@ def lib():
             "jfnk_step": (I, [P, P, D, D, D, ctypes.POINTER(jfnk_stats)]),
             "jfnk_dt_from_cfl": (I, [P, P, D, DP]),
             "jfnk_set_profiling": (I, [P, I]),
+            "jfnk_residual_noalloc": (I, [P, P, P, D, P]),
             "jfnk_last_error": (ctypes.c_char_p, [P]),
             "jfnk_destroy": (None, [P]),
         }
@@ -122,7 +123,7 @@ def lib():
 EXPORTED = ["jfnk_default_options", "jfnk_create", "jfnk_workspace_bytes", "jfnk_bind", "jfnk_vector_length",
             "jfnk_set_options", "jfnk_residual", "jfnk_scaling", "jfnk_jv", "jfnk_precond_apply",
             "jfnk_linear_solve", "jfnk_step", "jfnk_dt_from_cfl", "jfnk_set_profiling", "jfnk_last_error",
-            "jfnk_destroy"]
+            "jfnk_destroy", "jfnk_residual_noalloc"]
 
 
 class JFNKError(RuntimeError):
@@ -215,6 +216,13 @@ class Solver:
     def residual(self, X: torch.Tensor, Xn: torch.Tensor, dt: float, out: Optional[torch.Tensor] = None):
         F = self._vec() if out is None else out
         self._check(lib().jfnk_residual(self.h, _ptr(X), _ptr(Xn), dt, _ptr(F)))
+        return F
+
+    def residual_noalloc(self, X: torch.Tensor, Xn: torch.Tensor, dt: float, out: Optional[torch.Tensor] = None):
+        """jfnk_residual_noalloc: the residual with the library's fixed scratch
+        (no workspace use, nothing allocated by the call)."""
+        F = self._vec() if out is None else out
+        self._check(lib().jfnk_residual_noalloc(self.h, _ptr(X), _ptr(Xn), dt, _ptr(F)))
         return F
 
     def scaling(self, X: torch.Tensor):

@@ -408,6 +408,11 @@ jfnk_status validate_options(jfnk_handle* h, const jfnk_options* o) {
 
 }  // namespace
 
+// accessors for the allocation-free entry point (noalloc.cu)
+const jfnk::Grid* jfnk_handle_grid(const jfnk_handle* h) { return &h->G; }
+cudaStream_t jfnk_handle_stream(const jfnk_handle* h) { return h->stream; }
+void jfnk_handle_set_error(jfnk_handle* h, const char* msg) { h->err = msg; }
+
 extern "C" {
 
 void jfnk_default_options(jfnk_options* o) {

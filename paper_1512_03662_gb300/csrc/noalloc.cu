@@ -1,0 +1,108 @@
+// jfnk_residual_noalloc: the residual entry point for callers that cannot
+// allocate device memory.
+//
+// jfnk_residual needs scratch (the X^n part b^n, p and T per cell, and the
+// face and momentum fluxes) that normally lives in the workspace the caller
+// allocates and binds.  Some callers cannot make that allocation: code that
+// runs where the process's device allocator belongs to another framework or
+// is locked down, plugins handed only the input and output buffers, or code
+// that must not trigger an allocation at that point of its run.  This entry
+// point keeps its scratch in a fixed array in the library's own device
+// memory instead, so it needs only the caller's input and output buffers and
+// a created handle (no jfnk_bind).
+//
+// The array is a file-scope __device__ variable: every GPU that loads the
+// library holds it (JFNK_NOALLOC_MAX_CELLS * 22 doubles, 11.5 MB) until the
+// process exits.  Host code reaches it only through the address returned by
+// cudaGetSymbolAddress, fetched once per device on the first call made with
+// that device current.  Every call shares the one array, so calls that
+// overlap on the GPU (different streams, or different host threads) race;
+// callers must serialise them.  No scratch needs clearing: each call writes
+// every scratch value before reading it.
+#include <cstdio>
+#include <string>
+
+#include "../../include/jfnk.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace jfnk;
+
+namespace {
+
+constexpr long long kNoallocFields = 22;   // 5 b^n + p + T + 3 Fm + 3 FE + 9 Psi (3D; 2D uses 14)
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) double g_noalloc_scratch[kNoallocFields * JFNK_NOALLOC_MAX_CELLS];
+
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device (fetched once).
+cudaError_t scratch_for_current_device(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = (double*)g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Grid and stream of a handle (defined with the handle in engine.cu).
+const jfnk::Grid* jfnk_handle_grid(const jfnk_handle* h);
+cudaStream_t jfnk_handle_stream(const jfnk_handle* h);
+void jfnk_handle_set_error(jfnk_handle* h, const char* msg);
+
+extern "C" jfnk_status jfnk_residual_noalloc(jfnk_handle* h, const double* X, const double* Xn, double dt,
+                                             double* F) {
+    if (!h) return JFNK_EINVAL;
+    if (!X || !Xn || !F || !(dt > 0.0)) {
+        jfnk_handle_set_error(h, "bad arguments to jfnk_residual_noalloc");
+        return JFNK_EINVAL;
+    }
+    const Grid& G = *jfnk_handle_grid(h);
+    if (G.ncell > JFNK_NOALLOC_MAX_CELLS) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "jfnk_residual_noalloc: %lld cells exceed the fixed scratch limit of %d cells",
+                 G.ncell, JFNK_NOALLOC_MAX_CELLS);
+        jfnk_handle_set_error(h, buf);
+        return JFNK_EINVAL;
+    }
+    double* base = nullptr;
+    cudaError_t e = scratch_for_current_device(&base);
+    if (e != cudaSuccess) {
+        std::string m = std::string("jfnk_residual_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+        jfnk_handle_set_error(h, m.c_str());
+        return JFNK_ECUDA;
+    }
+    const long long nc = G.ncell, nd = G.ndim;
+    double* bn = base;
+    double* p = bn + (2 + nd) * nc;
+    double* T = p + nc;
+    double* Fm = T + nc;
+    double* FE = Fm + nd * nc;
+    double* Psi = FE + nd * nc;
+    cudaStream_t s = jfnk_handle_stream(h);
+    launch_eos(G, Xn, p, T, s);
+    launch_fluxes(G, Xn, p, T, Fm, FE, Psi, s);
+    launch_assemble<kModeBn, double>(G, Xn, p, Fm, FE, Psi, nullptr, nullptr, nullptr, nullptr, 0, dt, bn,
+                                     (double*)nullptr, s);
+    launch_eos(G, X, p, T, s);
+    launch_fluxes(G, X, p, T, Fm, FE, Psi, s);
+    launch_assemble<kModeRes, double>(G, X, p, Fm, FE, Psi, bn, nullptr, nullptr, nullptr, 0, dt, F,
+                                      (double*)nullptr, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        std::string m = std::string("jfnk_residual_noalloc: ") + cudaGetErrorString(e);
+        jfnk_handle_set_error(h, m.c_str());
+        return JFNK_ECUDA;
+    }
+    return JFNK_OK;
+}
