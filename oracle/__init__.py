@@ -22,6 +22,9 @@ Modules
                   sound-wave + thermal-diffusion systems in delta form, a
                   geometric multigrid V-cycle for them and a sparse direct
                   solve used as the exact reference.
+  adjoint         Gradients through one implicit step: vector-Jacobian
+                  products of the residual (reverse-mode derivatives of the
+                  discretisation above) and the transposed Newton-system solve.
 
 Readings of points the paper leaves open are stated where they are used.
 """
