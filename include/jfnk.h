@@ -177,6 +177,25 @@ jfnk_status jfnk_linear_solve(jfnk_handle* h, const double* X, const double* Xn,
 jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, double krylov_tol,
                       jfnk_stats* stats);
 
+/* Vector-Jacobian product of the residual (the benchmark spec's adjoint kernel;
+ * the paper has no adjoint): y = (dG/dX)^T w at X with G = U/dt - theta R_U,
+ * i.e. the transpose of dF_U/dX of Eq. crank_nicholson.  Double vectors,
+ * packed; wall slots of y are zero.  Hand-written reverse of the residual
+ * kernels; atomic accumulation makes y reproducible to round-off only. */
+jfnk_status jfnk_vjp_residual(jfnk_handle* h, const double* X, double dt, const double* w, double* y);
+
+/* Adjoint of one implicit step (needs an FP64 handle).  Given the step's
+ * input Xn and converged output Xnp1 and the gradient gbar of a loss with
+ * respect to Xnp1, solves J^T lam = gbar (J = dG/dX at Xnp1; scaled as in Eq.
+ * jacobian_system_norm, GMRES with the options' eta and restart, right-
+ * preconditioned by the transpose of the physics-based preconditioner with
+ * transposed multigrid cycles) and returns gXn = (db^n/dXn)^T lam and, in
+ * *gK0 (host, may be NULL), theta lam.dR/dK0(Xnp1) + (1-theta) lam.dR/dK0(Xn).
+ * dt is held fixed.  JFNK_ENOCONV_GMRES if the transposed solve stopped at
+ * gmres_max_it (outputs from the last iterate). */
+jfnk_status jfnk_vjp(jfnk_handle* h, const double* Xn, const double* Xnp1, double dt, const double* gbar, double* gXn,
+                     double* gK0, jfnk_stats* stats);
+
 /* dt = cfl * min_d dx_d / max(|u_cell| + c_s) (Sect. 1, CFL_hydro), u_cell the
  * mean of the two face velocities per direction.  *dt is host. */
 jfnk_status jfnk_dt_from_cfl(jfnk_handle* h, const double* X, double cfl, double* dt);

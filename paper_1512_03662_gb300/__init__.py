@@ -109,6 +109,8 @@ def lib():
             "jfnk_dt_from_cfl": (I, [P, P, D, DP]),
             "jfnk_set_profiling": (I, [P, I]),
             "jfnk_residual_noalloc": (I, [P, P, P, D, P]),
+            "jfnk_vjp_residual": (I, [P, P, D, P, P]),
+            "jfnk_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(jfnk_stats)]),
             "jfnk_last_error": (ctypes.c_char_p, [P]),
             "jfnk_destroy": (None, [P]),
         }
@@ -123,7 +125,7 @@ def lib():
 EXPORTED = ["jfnk_default_options", "jfnk_create", "jfnk_workspace_bytes", "jfnk_bind", "jfnk_vector_length",
             "jfnk_set_options", "jfnk_residual", "jfnk_scaling", "jfnk_jv", "jfnk_precond_apply",
             "jfnk_linear_solve", "jfnk_step", "jfnk_dt_from_cfl", "jfnk_set_profiling", "jfnk_last_error",
-            "jfnk_destroy", "jfnk_residual_noalloc"]
+            "jfnk_destroy", "jfnk_residual_noalloc", "jfnk_vjp_residual", "jfnk_vjp"]
 
 
 class JFNKError(RuntimeError):
@@ -257,7 +259,52 @@ class Solver:
         d["status"] = code
         return d
 
+    def vjp_residual(self, X: torch.Tensor, dt: float, w: torch.Tensor) -> torch.Tensor:
+        """jfnk_vjp_residual: (dG/dX)^T w at X."""
+        y = self._vec()
+        self._check(lib().jfnk_vjp_residual(self.h, _ptr(X), dt, _ptr(w), _ptr(y)))
+        return y
+
+    def vjp(self, Xn: torch.Tensor, Xnp1: torch.Tensor, dt: float, gbar: torch.Tensor):
+        """jfnk_vjp: gradients through one implicit step; returns
+        (dL/dXn, dL/dK0, stats, status)."""
+        gXn = self._vec()
+        gK0 = ctypes.c_double()
+        st = jfnk_stats()
+        code = self._check(lib().jfnk_vjp(self.h, _ptr(Xn), _ptr(Xnp1), dt, _ptr(gbar), _ptr(gXn),
+                                          ctypes.byref(gK0), ctypes.byref(st)), allow_positive=True)
+        return gXn, gK0.value, st.as_dict(), code
+
     def dt_from_cfl(self, X: torch.Tensor, cfl: float) -> float:
         dt = ctypes.c_double()
         self._check(lib().jfnk_dt_from_cfl(self.h, _ptr(X), cfl, ctypes.byref(dt)))
         return dt.value
+
+
+class JFNKStep(torch.autograd.Function):
+    """One implicit step X^n -> X^{n+1} as a differentiable operation.
+
+    forward runs jfnk_step on a copy of X^n; backward solves the transposed
+    Newton system with jfnk_vjp (no unrolling of the Newton iterations) and
+    returns the gradients with respect to X^n and to the conductivity
+    prefactor K0 (passed as a 0-dim tensor equal to the solver's K0; the
+    solver's K0 is what the step uses).  One checkpoint (X^n and X^{n+1}) is
+    kept per step.  dt is held fixed."""
+
+    @staticmethod
+    def forward(ctx, Xn, K0, solver, dt, newton_tol=0.0, krylov_tol=0.0):
+        X = Xn.detach().clone()
+        st = solver.step(X, dt, newton_tol, krylov_tol)
+        if st["status"] != JFNK_OK:
+            raise JFNKError(st["status"], "implicit step did not converge")
+        ctx.solver, ctx.dt = solver, dt
+        ctx.save_for_backward(Xn.detach(), X)
+        return X
+
+    @staticmethod
+    def backward(ctx, gbar):
+        Xn, Xnp1 = ctx.saved_tensors
+        gXn, gK0, st, code = ctx.solver.vjp(Xn, Xnp1, ctx.dt, gbar.contiguous().double())
+        if code != JFNK_OK:
+            raise JFNKError(code, "transposed solve did not converge")
+        return gXn, torch.tensor(gK0, dtype=torch.float64, device=gbar.device), None, None, None, None

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libjfnk.so")
-SOURCES = ["residual.cu", "krylov.cu", "precond.cu", "engine.cu", "noalloc.cu"]
+SOURCES = ["residual.cu", "krylov.cu", "precond.cu", "adjoint.cu", "engine.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

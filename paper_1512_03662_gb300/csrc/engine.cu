@@ -37,6 +37,9 @@ struct jfnk_handle {
     double *bn, *G0, *L, *R, *Linv, *Rinv, *Xp, *dxh, *p, *T, *Fm, *FE, *Psi, *partials, *scal;
     double *H, *cs, *sn, *g, *y, *vscale, *hc2;
     void *V, *Z, *rp, *re, *ru, *C;
+    // adjoint (FP64): VJP scratch, its output, transposed-preconditioner
+    // temporaries, right-hand side, multiplier and a scaled input vector
+    double *adj, *Xb, *rub, *reb, *rpb, *b64, *lam, *w64;
     long long npartials;
     std::vector<MGLevel> levels;
     size_t elt;        // bytes per basis element
@@ -61,6 +64,8 @@ jfnk_status fail(jfnk_handle* h, jfnk_status st, const char* fmt, ...) {
         cudaError_t e_ = (call);                                                               \
         if (e_ != cudaSuccess) return fail(h, JFNK_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
+
+#define CUDA_CHECK_VOID(call) (void)(call)
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -98,6 +103,14 @@ size_t plan(jfnk_handle* h, char* base) {
     h->y = (double*)take(m * 8);
     h->vscale = (double*)take((m + 1) * 8);
     h->hc2 = (double*)take((m + 1) * 8);
+    h->adj = (double*)take(vjp_scratch_doubles(h->G) * 8);
+    h->Xb = (double*)take(nv * 8);
+    h->rub = (double*)take(nd * nc * 8);
+    h->reb = (double*)take(nc * 8);
+    h->rpb = (double*)take(nc * 8);
+    h->b64 = (double*)take(nv * 8);
+    h->lam = (double*)take(nv * 8);
+    h->w64 = (double*)take(nv * 8);
     const size_t e = h->elt;
     h->V = take((size_t)(m + 1) * nv * e);
     h->Z = take((size_t)m * nv * e);
@@ -111,6 +124,7 @@ size_t plan(jfnk_handle* h, char* base) {
             L.K = take((size_t)h->nf * nd * L.ncell * e);
             L.x = take((size_t)h->nf * L.ncell * e);
             L.rhs = take((size_t)h->nf * L.ncell * e);
+            L.r = take((size_t)h->nf * L.ncell * e);
         }
     }
     return off;
@@ -189,24 +203,25 @@ void si_setup(jfnk_handle* h, const double* X, double dt) {
     }
 }
 
+// one V-cycle from level l; tr = 1 solves the transposed system
 template <typename T>
-void vcycle(jfnk_handle* h, size_t l) {
+void vcycle(jfnk_handle* h, size_t l, int tr = 0) {
     cudaStream_t s = h->stream;
     auto& Lv = h->levels;
     if (l + 1 == Lv.size()) {
-        launch_coarsest<T>(h->nf, Lv[l], s);
+        launch_coarsest<T>(h->nf, Lv[l], s, tr);
         return;
     }
     for (int k = 0; k < h->opt.mg_nu1; ++k) {
-        launch_smooth<T>(h->G, h->nf, Lv[l], 0, s);
-        launch_smooth<T>(h->G, h->nf, Lv[l], 1, s);
+        launch_smooth<T>(h->G, h->nf, Lv[l], 0, s, tr);
+        launch_smooth<T>(h->G, h->nf, Lv[l], 1, s, tr);
     }
-    launch_restrict<T>(h->G, h->nf, Lv[l], Lv[l + 1], s);
-    vcycle<T>(h, l + 1);
+    launch_restrict<T>(h->G, h->nf, Lv[l], Lv[l + 1], s, tr);
+    vcycle<T>(h, l + 1, tr);
     launch_prolong<T>(h->G, h->nf, Lv[l], Lv[l + 1], s);
     for (int k = 0; k < h->opt.mg_nu2; ++k) {
-        launch_smooth<T>(h->G, h->nf, Lv[l], 1, s);
-        launch_smooth<T>(h->G, h->nf, Lv[l], 0, s);
+        launch_smooth<T>(h->G, h->nf, Lv[l], 1, s, tr);
+        launch_smooth<T>(h->G, h->nf, Lv[l], 0, s, tr);
     }
 }
 
@@ -391,6 +406,114 @@ template <typename T>
 jfnk_status newton_solve(jfnk_handle* h, const double* X, double dt, double eta, SolveOut& so) {
     linearize<T>(h, X, dt);
     return gmres<T>(h, X, dt, eta, so);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (FP64 handles)
+// ---------------------------------------------------------------------------
+
+// out = (a dU/dX + b dR/dX)^T w at Xs
+void vjp_apply(jfnk_handle* h, const double* Xs, const double* w, double a, double b, double* out) {
+    cudaStream_t s = h->stream;
+    launch_eos(h->G, Xs, h->p, h->T, s);
+    launch_face_fluxes(h->G, Xs, h->p, h->T, h->Fm, h->FE, s);
+    launch_vjp(h->G, Xs, h->p, h->T, h->Fm, w, a, b, h->adj, out, s);
+}
+
+// z = M^-T y (transpose of the scaled physics-based preconditioner)
+void precond_T(jfnk_handle* h, double dt, const double* y, double* z) {
+    cudaStream_t s = h->stream;
+    if (h->nf == 0) {
+        CUDA_CHECK_VOID(cudaMemcpyAsync(z, y, h->nvec * 8, cudaMemcpyDeviceToDevice, s));
+        return;
+    }
+    launch_precondT_out(h->G, (const double*)h->C, dt, h->nf, y, h->rub, h->reb, h->rpb, h->levels[0], s);
+    for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<double>(h, 0, 1);
+    launch_precondT_in(h->G, (const double*)h->C, h->nf, h->levels[0], h->rub, h->reb, h->rpb, z, s);
+}
+
+// out = J^T z in scaled form: R (dG/dX)^T (L^-1 z) at Xs
+void jT_apply(jfnk_handle* h, const double* Xs, double dt, const double* z, double* out) {
+    cudaStream_t s = h->stream;
+    launch_mul(h->Linv, z, h->w64, h->nvec, s);
+    vjp_apply(h, Xs, h->w64, 1.0 / dt, -h->opt.theta, h->Xb);
+    launch_mul(h->R, h->Xb, out, h->nvec, s);
+}
+
+// Restarted GMRES on J^T M^-T (right preconditioned), RHS in V[0] and b64.
+jfnk_status gmres_adj(jfnk_handle* h, const double* X, double dt, double eta, SolveOut& so) {
+    cudaStream_t s = h->stream;
+    const int m = h->opt.gmres_m;
+    const int ldh = m + 1;
+    const long long n = h->nvec;
+    jfnk_status st;
+    double* V = (double*)h->V;
+    double* Z = (double*)h->Z;
+    launch_zero<double>(h->dxh, n, s);
+    launch_norm2_partials<double>(V, n, h->partials, s);
+    launch_finalize(h->partials, kRedBlocks, h->scal, kSlotBeta, 0, s);
+    if ((st = sync_read(h)) != JFNK_OK) return st;
+    const double beta0 = h->hpin[kSlotBeta];
+    so.beta0 = beta0;
+    if (!std::isfinite(beta0)) return fail(h, JFNK_ENONFINITE, "non-finite adjoint right-hand side");
+    if (beta0 == 0.0) {
+        so.converged = 1;
+        return JFNK_OK;
+    }
+    int total = 0;
+    double res = beta0;
+    for (;;) {
+        launch_init_cycle(h->scal, h->g, h->vscale, m, s);
+        int k = 0;
+        bool done = false;
+        for (int j = 0; j < m; ++j) {
+            if (total >= h->opt.gmres_max_it) break;
+            double* Vj = V + (long long)j * n;
+            double* Zj = Z + (long long)j * n;
+            double* Vn = V + (long long)(j + 1) * n;
+            launch_scale_copy<double, double>(Vj, 1.0, h->vscale, j, 0, h->w64, n, s);
+            precond_T(h, dt, h->w64, Zj);
+            jT_apply(h, X, dt, Zj, Vn);
+            double* hcol = h->H + (long long)j * ldh;
+            launch_multidot<double>(V, n, j + 1, Vn, n, h->partials, s);
+            launch_multidot_finalize(h->partials, kRedBlocks, j + 1, h->vscale, hcol, 0, s);
+            launch_axpy_norm<double>(Vn, V, n, j + 1, hcol, h->vscale, n, h->partials, s);
+            if (h->opt.reorth) {
+                launch_multidot<double>(V, n, j + 1, Vn, n, h->partials, s);
+                launch_multidot_finalize(h->partials, kRedBlocks, j + 1, h->vscale, h->hc2, 0, s);
+                launch_axpy_norm<double>(Vn, V, n, j + 1, h->hc2, h->vscale, n, h->partials, s);
+                launch_add_col(hcol, h->hc2, j + 1, s);
+            }
+            launch_finalize(h->partials, kRedBlocks, h->scal, kSlotTmp, 0, s);
+            launch_set_subdiag(h->scal, hcol, j, h->vscale, s);
+            launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
+            if ((st = sync_read(h)) != JFNK_OK) return st;
+            so.jv++;
+            so.pc++;
+            total++;
+            k = j + 1;
+            res = h->hpin[kSlotRes];
+            const double hn = h->hpin[kSlotTmp];
+            if (!std::isfinite(res) || !std::isfinite(hn))
+                return fail(h, JFNK_ENONFINITE, "non-finite value in adjoint GMRES iteration %d", total);
+            if (hn == 0.0) { done = true; break; }
+            if (res < eta * beta0) { done = true; break; }
+        }
+        if (k > 0) {
+            launch_backsolve(h->H, ldh, k, h->g, h->y, s);
+            launch_update<double>(h->dxh, Z, n, k, h->y, n, s);
+        }
+        so.iterations = total;
+        so.res = res / beta0;
+        if (done || total >= h->opt.gmres_max_it || k == 0) {
+            so.converged = res < eta * beta0 ? 1 : 0;
+            return JFNK_OK;
+        }
+        jT_apply(h, X, dt, h->dxh, V);                 // restart from b - A x
+        launch_sub(h->b64, V, V, n, s);
+        launch_norm2_partials<double>(V, n, h->partials, s);
+        launch_finalize(h->partials, kRedBlocks, h->scal, kSlotBeta, 0, s);
+    }
 }
 
 jfnk_status validate_options(jfnk_handle* h, const jfnk_options* o) {
@@ -659,6 +782,62 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
     S->kernel_launches = g_launch_count - launches0;
     if (!S->converged && !h->opt.fixed_iterations) return JFNK_ENOCONV_NEWTON;
     (void)gmres_fail;
+    return JFNK_OK;
+}
+
+jfnk_status jfnk_vjp(jfnk_handle* h, const double* Xn, const double* Xnp1, double dt, const double* gbar, double* gXn,
+                     double* gK0, jfnk_stats* stats) {
+    jfnk_status st = check_bound(h);
+    if (st) return st;
+    if (!Xn || !Xnp1 || !gbar || !gXn || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_vjp");
+    if (h->mixed) return fail(h, JFNK_EINVAL, "jfnk_vjp needs an FP64 handle");
+    cudaStream_t s = h->stream;
+    const long long n = h->nvec;
+    scaling(h, Xnp1);
+    si_setup(h, Xnp1, dt);
+    double* V0 = (double*)h->V;
+    launch_mul(h->R, gbar, V0, n, s);
+    launch_mask_walls(h->G, V0, s);
+    CUDA_TRY(h, cudaMemcpyAsync(h->b64, V0, n * 8, cudaMemcpyDeviceToDevice, s));
+    SolveOut so;
+    st = gmres_adj(h, Xnp1, dt, h->opt.eta, so);
+    if (st < 0) return st;
+    launch_mul(h->Linv, h->dxh, h->lam, n, s);
+    vjp_apply(h, Xn, h->lam, 1.0 / dt, 1.0 - h->opt.theta, gXn);
+    double gk = 0.0;
+    if (h->G.K0 != 0.0) {
+        const double wts[2] = {h->opt.theta, 1.0 - h->opt.theta};
+        const double* states[2] = {Xnp1, Xn};
+        for (int q = 0; q < 2; ++q) {
+            launch_eos(h->G, states[q], h->p, h->T, s);
+            launch_dRdK0_dot(h->G, h->T, h->lam, h->partials, s);
+            launch_finalize(h->partials, (int)cblocks(h), h->scal, kSlotTmp, 1, s);
+            if ((st = sync_read(h)) != JFNK_OK) return st;
+            gk += wts[q] * h->hpin[kSlotTmp];
+        }
+    } else {
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+    }
+    CUDA_TRY(h, cudaGetLastError());
+    if (gK0) *gK0 = gk;
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->newton_iterations = 1;
+        stats->gmres_iterations[0] = so.iterations;
+        stats->gmres_iterations_total = so.iterations;
+        stats->gmres_res[0] = so.res;
+        stats->gmres_converged[0] = so.converged;
+        stats->fhat_norm[0] = so.beta0;
+    }
+    return so.converged ? JFNK_OK : JFNK_ENOCONV_GMRES;
+}
+
+jfnk_status jfnk_vjp_residual(jfnk_handle* h, const double* X, double dt, const double* w, double* y) {
+    jfnk_status st = check_bound(h);
+    if (st) return st;
+    if (!X || !w || !y || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_vjp_residual");
+    vjp_apply(h, X, w, 1.0 / dt, -h->opt.theta, y);
+    CUDA_TRY(h, cudaGetLastError());
     return JFNK_OK;
 }
 

@@ -89,6 +89,7 @@ struct MGLevel {
     void* K;     // nf*ndim fields (coefficient on the lower face)
     void* x;     // nf fields
     void* rhs;   // nf fields
+    void* r;     // nf fields: residual scratch for the restriction
 };
 
 // per-cell coefficient fields of the preconditioner transforms
@@ -111,16 +112,33 @@ void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStr
 template <typename T>
 void launch_precond_in(const Grid& G, const T* C, const T* v, const double* vscale, int vslot, int nf, T* rp, T* re,
                        T* ru, MGLevel& L0, cudaStream_t s);
+// tr = 1: the transposed multigrid system (cell matrices transposed)
 template <typename T>
-void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s);
+void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr = 0);
 template <typename T>
-void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
+void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr = 0);
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
 template <typename T>
-void launch_coarsest(int nf, MGLevel& C, cudaStream_t s);
+void launch_coarsest(int nf, MGLevel& C, cudaStream_t s, int tr = 0);
 template <typename T>
 void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
                         const MGLevel& L0, T* z, double* partials, cudaStream_t s);
+
+// adjoint.cu
+// y = (a dU/dX + b dR/dX)^T w at X (p, T, half mass fluxes of X precomputed);
+// adj: vjp_scratch_doubles(G) doubles of scratch
+void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* Fmh, const double* w,
+                double a_u, double b_r, double* adj, double* Xb, cudaStream_t s);
+long long vjp_scratch_doubles(const Grid& G);
+// partial sums of w_E . (conduction divergence / K0) (T of the state given)
+void launch_dRdK0_dot(const Grid& G, const double* T, const double* w, double* partials, cudaStream_t s);
+void launch_precondT_out(const Grid& G, const double* C, double dt, int nf, const double* y, double* rub, double* reb,
+                         double* rpb, MGLevel& L0, cudaStream_t s);
+void launch_precondT_in(const Grid& G, const double* C, int nf, const MGLevel& L0, const double* rub,
+                        const double* reb, const double* rpb, double* z, cudaStream_t s);
+void launch_mul(const double* x, const double* y, double* out, long long n, cudaStream_t s);
+void launch_sub(const double* a, const double* b, double* out, long long n, cudaStream_t s);
+void launch_mask_walls(const Grid& G, double* v, cudaStream_t s);
 
 }  // namespace jfnk

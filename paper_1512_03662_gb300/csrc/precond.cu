@@ -44,8 +44,24 @@ template <typename T> __device__ __forceinline__ T ih2_of(const LvlDev& L, int d
 template <> __device__ __forceinline__ double ih2_of<double>(const LvlDev& L, int d) { return L.ih2[d]; }
 template <> __device__ __forceinline__ float ih2_of<float>(const LvlDev& L, int d) { return L.ih2f[d]; }
 
+// Storage index of cell (a,b,c) in a multigrid array.  With an even x extent
+// the arrays are colour-split: all cells with i+j+k even first, then the odd
+// ones, each in x-fastest order (the two cells of an x pair share flat/2), so
+// a red-black half sweep reads and writes contiguous memory.  Levels with an
+// odd x extent (a single cell along x) keep the natural order.
+__device__ __forceinline__ long long rb_index(int n0, int n1, long long nc, int a, int b, int c) {
+    long long f = ((long long)c * n1 + b) * n0 + a;
+    if (n0 & 1) return f;
+    return (long long)((a + b + c) & 1) * (nc >> 1) + (f >> 1);
+}
+
 __device__ __forceinline__ long long lflat(const LvlDev& L, int a, int b, int c) {
-    return ((long long)c * L.n[1] + b) * L.n[0] + a;
+    return rb_index(L.n[0], L.n[1], L.nc, a, b, c);
+}
+
+// index of fine-level cell P in the level-0 multigrid arrays
+__device__ __forceinline__ long long mg0(const Grid& G, const Idx3& P) {
+    return rb_index(G.n[0], G.n[1], G.ncell, P.i[0], P.i[1], P.i[2]);
 }
 
 __device__ __forceinline__ int wrapi(int k, int n) { return k < 0 ? k + n : (k >= n ? k - n : k); }
@@ -116,13 +132,14 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
     double e = e_internal_at(G, X, P, 0, 0, 0);
     double p = G.gm1 * rho * e;
     Binv2 B = si_B(G, rho, p, dt, nf);
+    const long long mi = mg0(G, P);
     if (nf == 1) {
-        M[cc] = (T)((1.0 / dt) / B.bpp);
+        M[mi] = (T)((1.0 / dt) / B.bpp);
     } else {
-        M[0 * nc + cc] = (T)(B.b00 / dt);
-        M[1 * nc + cc] = (T)(B.b01 / dt);
-        M[2 * nc + cc] = (T)(B.b10 / dt);
-        M[3 * nc + cc] = (T)(B.b11 / dt);
+        M[0 * nc + mi] = (T)(B.b00 / dt);
+        M[1 * nc + mi] = (T)(B.b01 / dt);
+        M[2 * nc + mi] = (T)(B.b10 / dt);
+        M[3 * nc + mi] = (T)(B.b11 / dt);
     }
     const double cv = 1.0 / G.gm1;
     const double chi0 = (G.K0 != 0.0) ? conductivity_si(G, G.gm1 * e) : 0.0;
@@ -171,11 +188,11 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
         o[c] = -1;
         double rl = load_cell(G, X, P, o[0], o[1], o[2]);
         double rho_f = 0.5 * (rl + rho);
-        K[(0 * ND + c) * nc + cc] = (T)(m / rho_f);
+        K[(0 * ND + c) * nc + mi] = (T)(m / rho_f);
         if (nf == 2) {
             double chil = 0.0;
             if (G.K0 != 0.0) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
-            K[(1 * ND + c) * nc + cc] = (T)(m * (0.5 * (chil + chi0)) / cv);
+            K[(1 * ND + c) * nc + mi] = (T)(m * (0.5 * (chil + chi0)) / cv);
         }
         const double u = wall ? 0.0 : X[(2 + c) * nc + cc];
         C[(PcLu + c) * nc + cc] = (T)L[(2 + c) * nc + cc];
@@ -226,9 +243,8 @@ __device__ __forceinline__ double child_mean(const T* f, const LvlDev& F, const 
     for (int kz = 0; kz < nz; ++kz) {
         double ys[2];
         for (int ky = 0; ky < ny; ++ky) {
-            long long base = lflat(F, x0, y0 + ky, z0 + kz);
-            double v0 = (double)f[base];
-            ys[ky] = (nx == 2) ? (v0 + (double)f[base + 1]) / 2.0 : v0;
+            double v0 = (double)f[lflat(F, x0, y0 + ky, z0 + kz)];
+            ys[ky] = (nx == 2) ? (v0 + (double)f[lflat(F, x0 + 1, y0 + ky, z0 + kz)]) / 2.0 : v0;
         }
         zs[kz] = (ny == 2) ? (ys[0] + ys[1]) / 2.0 : ys[0];
     }
@@ -258,9 +274,8 @@ __global__ void k_coarsen(int nf, int ndim, LvlDev F, LvlDev C, const T* __restr
                 for (int kz = 0; kz < nz; ++kz) {
                     double ys[2];
                     for (int ky = 0; ky < ny; ++ky) {
-                        long long base = lflat(F, fx, fy + ky, fz + kz);
-                        double v0 = (double)k[base];
-                        ys[ky] = (nx == 2) ? (v0 + (double)k[base + 1]) / 2.0 : v0;
+                        double v0 = (double)k[lflat(F, fx, fy + ky, fz + kz)];
+                        ys[ky] = (nx == 2) ? (v0 + (double)k[lflat(F, fx + 1, fy + ky, fz + kz)]) / 2.0 : v0;
                     }
                     zs[kz] = (ny == 2) ? (ys[0] + ys[1]) / 2.0 : ys[0];
                 }
@@ -345,26 +360,27 @@ __global__ void k_precond_in(Grid G, const T* __restrict__ C, const T* __restric
 #pragma unroll
     for (int c = 0; c < ND; ++c) ru[c * nc + cc] = ruv[c];
     re[cc] = r_e;
+    const long long mi = mg0(G, P);
     if (sizeof(T) == 8) {
         // double: the oracle's order, r_p = dp/drho r_rho + dp/de r_e, rhs = B^-1 (r_p, r_e)
         T r_p = C[PcDpdrho * nc + cc] * r_rho + C[PcDpde * nc + cc] * r_e;
         rp[cc] = r_p;
         if (nf == 1) {
-            rhs[cc] = r_p * C[PcQ0 * nc + cc];
+            rhs[mi] = r_p * C[PcQ0 * nc + cc];
         } else {
-            rhs[cc] = C[PcQ0 * nc + cc] * r_p + C[PcQ1 * nc + cc] * r_e;
-            rhs[nc + cc] = C[PcQ2 * nc + cc] * r_p + C[PcQ3 * nc + cc] * r_e;
+            rhs[mi] = C[PcQ0 * nc + cc] * r_p + C[PcQ1 * nc + cc] * r_e;
+            rhs[nc + mi] = C[PcQ2 * nc + cc] * r_p + C[PcQ3 * nc + cc] * r_e;
         }
     } else {
         // float: folded coefficients (see PcQ*), free of cancellation
         T r_p = C[PcPr * nc + cc] * r_rho + C[PcPE * nc + cc] * r_E - C[PcDpde * nc + cc] * dot_ur;
         rp[cc] = r_p;
-        rhs[cc] = C[PcQ0 * nc + cc] * r_rho + C[PcQ1 * nc + cc] * r_E - C[PcQ2 * nc + cc] * dot_ur;
+        rhs[mi] = C[PcQ0 * nc + cc] * r_rho + C[PcQ1 * nc + cc] * r_E - C[PcQ2 * nc + cc] * dot_ur;
         if (nf == 2)
-            rhs[nc + cc] = C[PcQ3 * nc + cc] * r_rho + C[PcQ4 * nc + cc] * r_E - C[PcQ5 * nc + cc] * dot_ur;
+            rhs[nc + mi] = C[PcQ3 * nc + cc] * r_rho + C[PcQ4 * nc + cc] * r_E - C[PcQ5 * nc + cc] * dot_ur;
     }
-    x0[cc] = (T)0;
-    if (nf == 2) x0[nc + cc] = (T)0;
+    x0[mi] = (T)0;
+    if (nf == 2) x0[nc + mi] = (T)0;
 }
 
 template <typename T>
@@ -381,36 +397,53 @@ template void launch_precond_in<float>(const Grid&, const float*, const float*, 
 // multigrid
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+__device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+
+// Storage indices of the upper and lower neighbours of (a,b,c) along d
+// (periodic wrap; wall neighbours carry zero face coefficients).
+__device__ __forceinline__ void nb_index(const LvlDev& L, int d, int a, int b, int c, long long& ju, long long& jd) {
+    if (d == 0) {
+        ju = lflat(L, wrap_up(a, L.n[0]), b, c);
+        jd = lflat(L, wrap_dn(a, L.n[0]), b, c);
+    } else if (d == 1) {
+        ju = lflat(L, a, wrap_up(b, L.n[1]), c);
+        jd = lflat(L, a, wrap_dn(b, L.n[1]), c);
+    } else {
+        ju = lflat(L, a, b, wrap_up(c, L.n[2]));
+        jd = lflat(L, a, b, wrap_dn(c, L.n[2]));
+    }
+}
+
 // Red-black Gauss-Seidel half sweep over the cells of one colour (parity of
 // i+j+k).  With an even x extent each thread takes one cell of the colour
-// (compact mapping); otherwise threads of the other colour return.
-template <typename T, int NF>
-__global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
-                         const T* __restrict__ rhs, int colour, int compact) {
-    int i[3];
-    i[1] = blockIdx.y * blockDim.y + threadIdx.y;
-    i[2] = blockIdx.z;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (compact) i[0] = 2 * t + ((i[1] + i[2] + colour) & 1);
-    else i[0] = t;
-    if (i[0] >= Lv.n[0] || i[1] >= Lv.n[1]) return;
-    if (((i[0] + i[1] + i[2]) & 1) != colour) return;
-    const long long cc = lflat(Lv, i[0], i[1], i[2]);
+// (compact mapping); otherwise threads of the other colour return.  Loops
+// over directions and fields are unrolled at compile time (ND, NF) so all
+// per-thread arrays stay in registers.
+template <typename T, int NF, int ND>
+__global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
+                         const T* __restrict__ rhs, int colour, int compact, int tr) {
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    const int c = blockIdx.z;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = compact ? 2 * t + ((b + c + colour) & 1) : t;
+    if (a >= Lv.n[0] || b >= Lv.n[1]) return;
+    if (((a + b + c) & 1) != colour) return;
+    const long long cc = lflat(Lv, a, b, c);
     T dg[NF], of[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        dg[f] = (T)0;
-        of[f] = (T)0;
-        const T* xf = x + f * Lv.nc;
-        for (int d = 0; d < ndim; ++d) {
-            if (Lv.n[d] == 1) continue;
-            int up[3] = {i[0], i[1], i[2]}, dn[3] = {i[0], i[1], i[2]};
-            up[d] = wrapi(i[d] + 1, Lv.n[d]);
-            dn[d] = wrapi(i[d] - 1, Lv.n[d]);
-            long long ju = lflat(Lv, up[0], up[1], up[2]), jd = lflat(Lv, dn[0], dn[1], dn[2]);
-            const T* Kd = K + (f * ndim + d) * Lv.nc;
+    for (int f = 0; f < NF; ++f) { dg[f] = (T)0; of[f] = (T)0; }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        if (Lv.n[d] == 1) continue;
+        long long ju, jd;
+        nb_index(Lv, d, a, b, c, ju, jd);
+        const T ih2 = ih2_of<T>(Lv, d);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T* Kd = K + (long long)(f * ND + d) * Lv.nc;
+            const T* xf = x + (long long)f * Lv.nc;
             T Kl = Kd[cc], Ku = Kd[ju];
-            T ih2 = ih2_of<T>(Lv, d);
             dg[f] = dg[f] + (Kl + Ku) * ih2;
             of[f] = of[f] + (Ku * xf[ju] + Kl * xf[jd]) * ih2;
         }
@@ -418,7 +451,9 @@ __global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* 
     if (NF == 1) {
         x[cc] = (rhs[cc] + of[0]) / (M[cc] + dg[0]);
     } else {
-        T a11 = M[cc] + dg[0], a12 = M[Lv.nc + cc], a21 = M[2 * Lv.nc + cc], a22 = M[3 * Lv.nc + cc] + dg[NF - 1];
+        // tr: the transposed system (off-diagonal entries of the cell matrix swapped)
+        T m01 = M[Lv.nc + cc], m10 = M[2 * Lv.nc + cc];
+        T a11 = M[cc] + dg[0], a12 = tr ? m10 : m01, a21 = tr ? m01 : m10, a22 = M[3 * Lv.nc + cc] + dg[NF - 1];
         T b1 = rhs[cc] + of[0], b2 = rhs[Lv.nc + cc] + of[NF - 1];
         T det = a11 * a22 - a12 * a21;
         x[cc] = (a22 * b1 - a12 * b2) / det;
@@ -426,86 +461,96 @@ __global__ void k_smooth(int ndim, LvlDev Lv, const T* __restrict__ M, const T* 
     }
 }
 
+#define MG_DISPATCH(KERNEL, GRID, BLOCK, ...)                                                 \
+    do {                                                                                      \
+        ++g_launch_count;                                                                     \
+        if (nf == 1 && G.ndim == 3) KERNEL<T, 1, 3><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);      \
+        else if (nf == 1) KERNEL<T, 1, 2><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);                \
+        else if (G.ndim == 3) KERNEL<T, 2, 3><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);            \
+        else KERNEL<T, 2, 2><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);                             \
+    } while (0)
+
 template <typename T>
-void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s) {
+void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr) {
     int compact = (Lv.n[0] % 2 == 0) ? 1 : 0;
     int nx[3] = {compact ? Lv.n[0] / 2 : Lv.n[0], Lv.n[1], Lv.n[2]};
     CellLaunch cl = cell_launch(nx);
-    ++g_launch_count;
-    if (nf == 1)
-        k_smooth<T, 1><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
-                                                    (const T*)Lv.rhs, colour, compact);
-    else
-        k_smooth<T, 2><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x,
-                                                    (const T*)Lv.rhs, colour, compact);
+    MG_DISPATCH(k_smooth, cl.grid, cl.block, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x, (const T*)Lv.rhs,
+                colour, compact, tr);
 }
-template void launch_smooth<double>(const Grid&, int, MGLevel&, int, cudaStream_t);
-template void launch_smooth<float>(const Grid&, int, MGLevel&, int, cudaStream_t);
+template void launch_smooth<double>(const Grid&, int, MGLevel&, int, cudaStream_t, int);
+template void launch_smooth<float>(const Grid&, int, MGLevel&, int, cudaStream_t, int);
 
 // residual rhs - A x at fine cell (a,b,c), field f
-template <typename T, int NF>
-__device__ __forceinline__ T fine_residual(int ndim, const LvlDev& F, const T* M, const T* K, const T* x, const T* rhs,
-                                           int f, int a, int b, int c) {
-    long long cc = lflat(F, a, b, c);
+template <typename T, int NF, int ND>
+__device__ __forceinline__ T fine_residual(const LvlDev& F, const T* M, const T* K, const T* x, const T* rhs, int f,
+                                           int a, int b, int c, int tr) {
+    const long long cc = lflat(F, a, b, c);
     T out;
     if (NF == 1) out = M[cc] * x[cc];
-    else out = M[(f * 2 + 0) * F.nc + cc] * x[cc] + M[(f * 2 + 1) * F.nc + cc] * x[F.nc + cc];
-    const T* xf = x + f * F.nc;
-    int i[3] = {a, b, c};
-    for (int d = 0; d < ndim; ++d) {
+    else if (!tr) out = M[(f * 2 + 0) * F.nc + cc] * x[cc] + M[(f * 2 + 1) * F.nc + cc] * x[F.nc + cc];
+    else out = M[(0 * 2 + f) * F.nc + cc] * x[cc] + M[(1 * 2 + f) * F.nc + cc] * x[F.nc + cc];
+    const T* xf = x + (long long)f * F.nc;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
         if (F.n[d] == 1) continue;
-        int up[3] = {a, b, c}, dn[3] = {a, b, c};
-        up[d] = wrapi(i[d] + 1, F.n[d]);
-        dn[d] = wrapi(i[d] - 1, F.n[d]);
-        long long ju = lflat(F, up[0], up[1], up[2]), jd = lflat(F, dn[0], dn[1], dn[2]);
-        const T* Kd = K + (f * ndim + d) * F.nc;
+        long long ju, jd;
+        nb_index(F, d, a, b, c, ju, jd);
+        const T* Kd = K + (long long)(f * ND + d) * F.nc;
         T Kl = Kd[cc], Ku = Kd[ju];
         out = out - (Ku * (xf[ju] - xf[cc]) - Kl * (xf[cc] - xf[jd])) * ih2_of<T>(F, d);
     }
-    return rhs[f * F.nc + cc] - out;
+    return rhs[(long long)f * F.nc + cc] - out;
 }
 
-template <typename T, int NF>
-__global__ void k_restrict(int ndim, LvlDev F, LvlDev C, const T* __restrict__ M, const T* __restrict__ K,
-                           const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ rhsc,
-                           T* __restrict__ xc) {
+// fine residual r = rhs - A x, one thread per fine cell
+template <typename T, int NF, int ND>
+__global__ void k_residual_mg(LvlDev F, const T* __restrict__ M, const T* __restrict__ K, const T* __restrict__ x,
+                             const T* __restrict__ rhs, T* __restrict__ r, int tr) {
+    int i[3];
+    long long cc;
+    if (!lvl_pos(F, i, cc)) return;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        r[(long long)f * F.nc + cc] = fine_residual<T, NF, ND>(F, M, K, x, rhs, f, i[0], i[1], i[2], tr);
+}
+
+// coarse right-hand side = mean of the children's residuals (pairs along x,
+// then y, then z); the coarse correction starts from zero
+template <typename T, int NF, int ND>
+__global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __restrict__ rhsc, T* __restrict__ xc) {
     int ic[3];
     long long cc;
     if (!lvl_pos(C, ic, cc)) return;
-    const int a = ic[0], b = ic[1], c = ic[2];
-    int cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
-    int nx = cd[0] ? 2 : 1, ny = cd[1] ? 2 : 1, nz = cd[2] ? 2 : 1;
-    int x0 = cd[0] ? 2 * a : a, y0 = cd[1] ? 2 * b : b, z0 = cd[2] ? 2 * c : c;
+    const bool cx = F.n[0] != C.n[0], cy = F.n[1] != C.n[1], cz = F.n[2] != C.n[2];
+    const int x0 = cx ? 2 * ic[0] : ic[0], y0 = cy ? 2 * ic[1] : ic[1], z0 = cz ? 2 * ic[2] : ic[2];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        T zs[2];
-        for (int kz = 0; kz < nz; ++kz) {
-            T ys[2];
-            for (int ky = 0; ky < ny; ++ky) {
-                T v0 = fine_residual<T, NF>(ndim, F, M, K, x, rhs, f, x0, y0 + ky, z0 + kz);
-                ys[ky] = (nx == 2) ? (v0 + fine_residual<T, NF>(ndim, F, M, K, x, rhs, f, x0 + 1, y0 + ky, z0 + kz)) / (T)2
-                                   : v0;
-            }
-            zs[kz] = (ny == 2) ? (ys[0] + ys[1]) / (T)2 : ys[0];
-        }
-        rhsc[f * C.nc + cc] = (nz == 2) ? (zs[0] + zs[1]) / (T)2 : zs[0];
-        xc[f * C.nc + cc] = (T)0;
+        const T* q = r + (long long)f * F.nc;
+        auto xm = [&](int yy, int zz) -> T {
+            T a = q[lflat(F, x0, yy, zz)];
+            return cx ? (a + q[lflat(F, x0 + 1, yy, zz)]) / (T)2 : a;
+        };
+        auto ym = [&](int zz) -> T {
+            T a = xm(y0, zz);
+            return cy ? (a + xm(y0 + 1, zz)) / (T)2 : a;
+        };
+        T a = ym(z0);
+        rhsc[(long long)f * C.nc + cc] = cz ? (a + ym(z0 + 1)) / (T)2 : a;
+        xc[(long long)f * C.nc + cc] = (T)0;
     }
 }
 
 template <typename T>
-void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
+void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr) {
+    CellLaunch fl = cell_launch(F.n);
+    MG_DISPATCH(k_residual_mg, fl.grid, fl.block, lvl(F), (const T*)F.M, (const T*)F.K, (const T*)F.x,
+                (const T*)F.rhs, (T*)F.r, tr);
     CellLaunch cl = cell_launch(C.n);
-    ++g_launch_count;
-    if (nf == 1)
-        k_restrict<T, 1><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
-                                                      (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
-    else
-        k_restrict<T, 2><<<cl.grid, cl.block, 0, s>>>(G.ndim, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
-                                                      (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, (T*)C.x);
+    MG_DISPATCH(k_restrict, cl.grid, cl.block, lvl(F), lvl(C), (const T*)F.r, (T*)C.rhs, (T*)C.x);
 }
-template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
-template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
+template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int);
+template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int);
 
 // coarse parents of fine index i along a coarsened direction
 __device__ __forceinline__ void parents(int i, int nc, int bc, int& par, int& oth) {
@@ -515,61 +560,51 @@ __device__ __forceinline__ void parents(int i, int nc, int bc, int& par, int& ot
     else if (oth < 0 || oth >= nc) oth = par;
 }
 
-template <typename T, int NF>
-__global__ void k_prolong(int ndim, int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
+template <typename T, int NF, int ND>
+__global__ void k_prolong(int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
                           T* __restrict__ xf) {
     int i[3];
     long long cc;
     if (!lvl_pos(F, i, cc)) return;
-    int bc[3] = {bc0, bc1, bc2};
-    int pa[3], ot[3], cd[3];
-    for (int d = 0; d < 3; ++d) {
-        cd[d] = F.n[d] != C.n[d];
-        if (cd[d]) parents(i[d], C.n[d], bc[d], pa[d], ot[d]);
-        else { pa[d] = i[d]; ot[d] = i[d]; }
-    }
+    const bool cx = F.n[0] != C.n[0], cy = F.n[1] != C.n[1], cz = F.n[2] != C.n[2];
+    int px = i[0], ox = i[0], py = i[1], oy = i[1], pz = i[2], oz = i[2];
+    if (cx) parents(i[0], C.n[0], bc0, px, ox);
+    if (cy) parents(i[1], C.n[1], bc1, py, oy);
+    if (cz) parents(i[2], C.n[2], bc2, pz, oz);
     const T w0 = (T)0.75, w1 = (T)0.25;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const T* q = xc + f * C.nc;
-        T vz[2];
-        int nz = cd[2] ? 2 : 1, ny = cd[1] ? 2 : 1;
-        for (int kz = 0; kz < nz; ++kz) {
-            int zz = kz == 0 ? pa[2] : ot[2];
-            T vy[2];
-            for (int ky = 0; ky < ny; ++ky) {
-                int yy = ky == 0 ? pa[1] : ot[1];
-                T a = q[lflat(C, pa[0], yy, zz)];
-                vy[ky] = cd[0] ? w0 * a + w1 * q[lflat(C, ot[0], yy, zz)] : a;
-            }
-            vz[kz] = cd[1] ? w0 * vy[0] + w1 * vy[1] : vy[0];
-        }
-        T v = cd[2] ? w0 * vz[0] + w1 * vz[1] : vz[0];
-        xf[f * F.nc + cc] = xf[f * F.nc + cc] + v;
+        const T* q = xc + (long long)f * C.nc;
+        // interpolate along x, then y, then z (the oracle's order)
+        auto along_x = [&](int yy, int zz) -> T {
+            T a = q[lflat(C, px, yy, zz)];
+            return cx ? w0 * a + w1 * q[lflat(C, ox, yy, zz)] : a;
+        };
+        auto along_y = [&](int zz) -> T {
+            T a = along_x(py, zz);
+            return cy ? w0 * a + w1 * along_x(oy, zz) : a;
+        };
+        T a = along_y(pz);
+        T v = cz ? w0 * a + w1 * along_y(oz) : a;
+        xf[(long long)f * F.nc + cc] = xf[(long long)f * F.nc + cc] + v;
     }
 }
 
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
     CellLaunch cl = cell_launch(F.n);
-    ++g_launch_count;
-    if (nf == 1)
-        k_prolong<T, 1><<<cl.grid, cl.block, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
-                                                     (const T*)C.x, (T*)F.x);
-    else
-        k_prolong<T, 2><<<cl.grid, cl.block, 0, s>>>(G.ndim, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C),
-                                                     (const T*)C.x, (T*)F.x);
+    MG_DISPATCH(k_prolong, cl.grid, cl.block, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C), (const T*)C.x, (T*)F.x);
 }
 template void launch_prolong<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
 template void launch_prolong<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
 
 template <typename T>
-__global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict__ rhs, T* __restrict__ x) {
+__global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict__ rhs, T* __restrict__ x, int tr) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (nf == 1) {
         x[0] = rhs[0] / M[0];
     } else {
-        T a11 = M[0], a12 = M[1], a21 = M[2], a22 = M[3];
+        T a11 = M[0], a12 = tr ? M[2] : M[1], a21 = tr ? M[1] : M[2], a22 = M[3];
         T det = a11 * a22 - a12 * a21;
         x[0] = (a22 * rhs[0] - a12 * rhs[1]) / det;
         x[1] = (a11 * rhs[1] - a21 * rhs[0]) / det;
@@ -577,12 +612,12 @@ __global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict_
 }
 
 template <typename T>
-void launch_coarsest(int nf, MGLevel& C, cudaStream_t s) {
+void launch_coarsest(int nf, MGLevel& C, cudaStream_t s, int tr) {
     ++g_launch_count;
-    k_coarsest<T><<<1, 32, 0, s>>>(nf, (const T*)C.M, (const T*)C.rhs, (T*)C.x);
+    k_coarsest<T><<<1, 32, 0, s>>>(nf, (const T*)C.M, (const T*)C.rhs, (T*)C.x, tr);
 }
-template void launch_coarsest<double>(int, MGLevel&, cudaStream_t);
-template void launch_coarsest<float>(int, MGLevel&, cudaStream_t);
+template void launch_coarsest<double>(int, MGLevel&, cudaStream_t, int);
+template void launch_coarsest<float>(int, MGLevel&, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // back substitution and transform out
@@ -598,8 +633,10 @@ __device__ __forceinline__ T du_at(const Grid& G, const T* C, T dt, const T* ru,
     int a = cell_map(Q.i[0] + o[0], G.n[0], G.bc[0]);
     int b = cell_map(Q.i[1] + o[1], G.n[1], G.bc[1]);
     int cz = cell_map(Q.i[2] + o[2], G.n[2], G.bc[2]);
-    long long jl = flat(G, a, b, cz);
-    return dt * (ru[c * nc + j] - C[(PcThf + c) * nc + j] * (dp[j] - dp[jl]));
+    Idx3 L;
+    L.i[0] = a; L.i[1] = b; L.i[2] = cz;
+    // dp lives in the (colour-split) multigrid array of level 0
+    return dt * (ru[c * nc + j] - C[(PcThf + c) * nc + j] * (dp[mg0(G, Q)] - dp[mg0(G, L)]));
 }
 
 template <int ND, typename T>
@@ -613,10 +650,11 @@ __global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int 
     if (cell_pos(G.n, P, cc)) {
         const long long nc = G.ncell;
         const T dt = (T)dt_d;
-        const T dp = x[cc];
+        const long long mi = mg0(G, P);
+        const T dp = x[mi];
         T de;
         if (nf == 1) de = dt * (re[cc] + (dp * (T)(1.0 / dt_d) - rp[cc]) * C[PcCde * nc + cc]);
-        else de = x[nc + cc];
+        else de = x[nc + mi];
         T du[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) du[c] = du_at<T>(G, C, dt, ru, x, c, P);

@@ -259,3 +259,4 @@ def test_nonfinite_state_is_reported(jf):
     with pytest.raises(jf.JFNKError) as e:
         S.step(_dev(X), 1e-3)
     assert e.value.status == jf.JFNK_ENONFINITE
+
