@@ -44,13 +44,13 @@ ETA = 1e-4
 # jv_kernels_128cubed.md): flops = dadd + dmul + 2 dfma, instructions =
 # dadd + dmul + dfma, both divided by the cell count.  Division sequences are
 # counted as the DFMA/DMUL/DADD instructions they execute.
-FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 3.0, "face_fluxes": 168.5, "mom_fluxes": 234.7, "assemble": 123.8}
-FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 3.0, "face_fluxes": 123.3, "mom_fluxes": 171.3, "assemble": 91.9}
+FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 3.0, "face_fluxes": 106.0, "mom_fluxes": 120.0, "assemble": 117.9}
+FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 3.0, "face_fluxes": 92.0, "mom_fluxes": 96.0, "assemble": 85.9}
 # DRAM bytes per cell per launch from the same capture (dram__bytes_read +
 # dram__bytes_write); at 128^3 part of the reads hit the 129 MB L2, so these
 # are lower bounds for 256^3 (where the algorithmic bytes below apply).
-DRAM_BYTES_PER_CELL_128 = {"perturb": 128.2, "eos": 16.2, "face_fluxes": 77.3, "mom_fluxes": 99.4,
-                           "assemble": 265.7}
+DRAM_BYTES_PER_CELL_128 = {"perturb": 128.2, "eos": 16.2, "face_fluxes": 76.8, "mom_fluxes": 98.8,
+                           "assemble": 265.6}
 JV_KERNELS = ["perturb", "eos", "face_fluxes", "mom_fluxes", "assemble"]
 # Algorithmic HBM bytes per cell of one launch of each Jv kernel (3D, FP64
 # state, FP32 Krylov vectors; each array the kernel must touch read or
@@ -163,9 +163,14 @@ def make_workload(n):
     return wl
 
 
+# solver options given on the command line (multigrid cycle shape); empty:
+# the library defaults
+OPT_OVERRIDES = {}
+
+
 def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
     import torch
-    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision)
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision, **OPT_OVERRIDES)
     S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
     X0 = torch.as_tensor(wl.X0, dtype=torch.float64, device=device)
     X = X0.clone()
@@ -193,7 +198,7 @@ def e2e_arm(jf, wl, precision, steps, device, stream):
     the state from pinned host memory to the device, steps, and copies the
     new state back."""
     import torch
-    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision)
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision, **OPT_OVERRIDES)
     S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
     host = torch.as_tensor(wl.X0, dtype=torch.float64).pin_memory()
     X = torch.empty_like(host, device=device)
@@ -270,7 +275,7 @@ def kernel_main(args):
     wl = make_workload(args.n)
     prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
     # a single Jv or preconditioner call needs no Krylov basis: restart length 1
-    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, gmres_m=1)
+    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, gmres_m=1, **OPT_OVERRIDES)
     S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
     X = torch.as_tensor(wl.X0, dtype=torch.float64, device=device)
     dt = S.dt_from_cfl(X, wl.cfl_hydro)
@@ -305,7 +310,13 @@ def main():
     ap.add_argument("--only", choices=["jv", "precond"], default=None,
                     help="time only repeated Jv or preconditioner calls (profiling)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--mg-cycles", type=int, default=None, help="multigrid V-cycles per preconditioner apply")
+    ap.add_argument("--mg-nu1", type=int, default=None, help="pre-smoothing sweeps")
+    ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     args = ap.parse_args()
+    for k in ("mg_cycles", "mg_nu1", "mg_nu2"):
+        if getattr(args, k) is not None:
+            OPT_OVERRIDES[k] = getattr(args, k)
     if args.only:
         kernel_main(args)
         return
@@ -332,6 +343,9 @@ def main():
     barrier(ws)
     clocks.start()
     S, X0, dt, ms_mixed, st_mixed = run_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream, True)
+    so = S.options
+    solver_cfg = {"newton_tol": NEWTON_TOL, "eta": ETA, "gmres_m": so.gmres_m, "precond": so.precond,
+                  "mg_cycles": so.mg_cycles, "mg_nu1": so.mg_nu1, "mg_nu2": so.mg_nu2}
     barrier(ws)
     clk = clocks.stop()
     ms_mixed = max_over_ranks(ws, ms_mixed)
@@ -364,12 +378,18 @@ def main():
     tinst = FP64_INST_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e12
     hbm_gbs = HBM_BYTES_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e9
     scale = wl.ncell / 128 ** 3
-    roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+    # The kernel is bound by the FP64 pipe, which issues one DADD, DMUL or DFMA
+    # per lane slot whatever its flop count, so the roofline is stated in FP64
+    # instructions per second against the issue peak; the flop rate (DFMA = 2)
+    # is reported beside it.
+    roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": tinst, "peak": FP64_PEAK_TINST,
+                "unit": "T FP64 inst/s", "frac": tinst / FP64_PEAK_TINST,
                 "traffic": DRAM_BYTES_PER_CELL_128[name] * 128 ** 3 * scale,
                 "traffic_note": "ncu DRAM bytes of a 128^3 launch scaled by the cell ratio",
-                "peak_src": "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "fp64_issue_tinst_s": tinst, "fp64_issue_frac": tinst / FP64_PEAK_TINST,
+                "peak_src": "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz",
+                "fp64_inst_per_cell": FP64_INST_PER_CELL[name],
+                "achieved_tflops": achieved_tflops, "peak_tflops": FP64_PEAK_TFLOPS,
+                "frac_tflops": achieved_tflops / FP64_PEAK_TFLOPS,
                 "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"],
                 "algorithmic_bytes_per_cell": HBM_BYTES_PER_CELL[name]}
 
@@ -397,7 +417,7 @@ def main():
                 "config": {"workload": f"convbox3d {args.n}^3 (problem 4), CFL_hydro {wl.cfl_hydro:g}, "
                                        f"dt {dt:.4g}", "global_batch": 1, "seq_len": 0,
                            "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "state (670 MB/vector) larger than L2, no flush"},
+                           "l2": "state (670 MB/vector) larger than L2, no flush", "solver": solver_cfg},
                 "jv_gcell_s": njv * wl.ncell / (jv_ms / 1e3) / 1e9 if jv_ms > 0 else None,
                 "newton_per_step": sum(s["newton_iterations"] for s in st_mixed) / len(st_mixed),
                 "gmres_per_newton": sum(s["gmres_iterations_total"] for s in st_mixed) /

@@ -91,10 +91,10 @@ __device__ __forceinline__ UpwindD upwind_d(double q_near, double q_far, double 
 }
 
 __device__ __forceinline__ double cond_chi(const Grid& G, double T) {
-    return G.chi_exp == 3.0 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+    return G.chi3 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
 }
 __device__ __forceinline__ double cond_dchi(const Grid& G, double T) {
-    return G.chi_exp == 3.0 ? 3.0 * G.K0 * (T * T) : G.K0 * G.chi_exp * pow(T, G.chi_exp - 1.0);
+    return G.chi3 ? 3.0 * G.K0 * (T * T) : G.K0 * G.chi_exp * pow(T, G.chi_exp - 1.0);
 }
 
 struct AdjBufs {
@@ -145,7 +145,7 @@ __global__ void k_vjp_assemble(Grid G, const double* __restrict__ X, const doubl
             long long js;
             double sg;
             if (normal_slot(G, d, P, o[0], o[1], o[2], js, sg)) atomicAdd(A.Xb + (2 + d) * nc + js, -sg * RE * pc * G.idx[d]);
-        } else if (G.g[d] != 0.0) {
+        } else if (((G.gmask >> d) & 1)) {
             atomicAdd(A.Fmhb + d * nc + cc, RE * G.g[d]);
             if (hasup) atomicAdd(A.Fmhb + d * nc + ju, RE * G.g[d]);
         }
@@ -164,7 +164,7 @@ __global__ void k_vjp_assemble(Grid G, const double* __restrict__ X, const doubl
         const double uc = X[(2 + c) * nc + cc];
         const double rho_f = 0.5 * (X[jl] + rho);
         double rfb = Uu * uc;                              // adjoint of rho_f
-        if (G.g[c] != 0.0) rfb += Ru * G.g[c];
+        if (((G.gmask >> c) & 1)) rfb += Ru * G.g[c];
         rhob += 0.5 * rfb;
         atomicAdd(A.Xb + jl, 0.5 * rfb);
         atomicAdd(A.Xb + (2 + c) * nc + cc, Uu * rho_f);
@@ -294,7 +294,7 @@ __global__ void k_vjp_face(Grid G, const double* __restrict__ X, const double* _
                 atomicAdd(A.pb + c, 0.5 * feb * u);
             }
         }
-        if (G.K0 != 0.0) {
+        if (G.has_cond) {
             // FE contains -q, q = (chi_L + chi_R)/2 (T_R - T_L) / dx
             const double qb = -feb;
             const double Tl = T[jl], Tc = T[c];
@@ -321,7 +321,7 @@ __global__ void k_vjp_eos(Grid G, const double* __restrict__ X, const double* __
     const double Tc = T[cc];
     const double e = Tc / G.gm1;
     double Tbt = A.Tb[cc];
-    if (G.K0 != 0.0) Tbt += A.chib[cc] * cond_dchi(G, Tc);
+    if (G.has_cond) Tbt += A.chib[cc] * cond_dchi(G, Tc);
     const double pbv = A.pb[cc];
     const double eb = pbv * G.gm1 * rho + Tbt * G.gm1;
     atomicAdd(A.Xb + cc, pbv * G.gm1 * e);
@@ -358,14 +358,14 @@ __global__ void k_dRdK0_dot(Grid G, const double* __restrict__ T, const double* 
             o[d] = -1;
             const long long jl = cell_slot(G, P, o[0], o[1], o[2]);
             const double Tl = T[jl], Tc = T[cc];
-            const double kl = G.chi_exp == 3.0 ? Tl * Tl * Tl : pow(Tl, G.chi_exp);
-            const double kc = G.chi_exp == 3.0 ? Tc * Tc * Tc : pow(Tc, G.chi_exp);
+            const double kl = G.chi3 ? Tl * Tl * Tl : pow(Tl, G.chi_exp);
+            const double kc = G.chi3 ? Tc * Tc * Tc : pow(Tc, G.chi_exp);
             const double q0 = 0.5 * (kl + kc) * (Tc - Tl) * G.idx[d];
             double q1 = 0.0;
             long long ju;
             if (up_slot(G, d, P, ju)) {
                 const double Tu = T[ju];
-                const double ku = G.chi_exp == 3.0 ? Tu * Tu * Tu : pow(Tu, G.chi_exp);
+                const double ku = G.chi3 ? Tu * Tu * Tu : pow(Tu, G.chi_exp);
                 q1 = 0.5 * (kc + ku) * (Tu - Tc) * G.idx[d];
             }
             div = div + (q1 - q0) * G.idx[d];

@@ -9,6 +9,7 @@ namespace jfnk {
 
 constexpr int kBlock = 256;          // threads per block of the pointwise kernels
 constexpr int kRedBlocks = 1024;     // fixed block count of grid-stride reductions
+constexpr int kMaxRedBlocks = 2048;  // cap of the occupancy-sized reduction grids
 
 struct Grid {
     int ndim;
@@ -21,7 +22,19 @@ struct Grid {
     double K0, chi_exp;
     int energy_form;                 // 0 internal e, 1 total eps_t
     double theta;
+    // integer copies of the tests on the parameters above, so kernels branch
+    // on them without FP64 compares: bit d of gmask = (g[d] != 0),
+    // has_cond = (K0 != 0), chi3 = (chi_exp == 3)
+    int gmask, has_cond, chi3;
 };
+
+inline void set_grid_flags(Grid& G) {
+    G.gmask = 0;
+    for (int d = 0; d < 3; ++d)
+        if (G.g[d] != 0.0) G.gmask |= 1 << d;
+    G.has_cond = G.K0 != 0.0;
+    G.chi3 = G.chi_exp == 3.0;
+}
 
 struct Idx3 { int i[3]; };
 
@@ -96,14 +109,14 @@ __device__ __forceinline__ double load_cell(const Grid& G, const double* __restr
 __device__ __forceinline__ double load_normal(const Grid& G, const double* __restrict__ u, int c, const Idx3& p,
                                               int o0, int o1, int o2) {
     int k[3] = {p.i[0] + o0, p.i[1] + o1, p.i[2] + o2};
-    double sgn = 1.0;
+    long long flip = 0;                 // sign-bit mask of the odd mirror
     for (int d = 0; d < 3; ++d) {
         if (d == c && G.bc[d] == 1) {
             int n = G.n[d];
             int kk = k[d];
             if (kk == 0 || kk == n) return 0.0;
-            if (kk < 0) { kk = -kk; sgn = -sgn; }
-            else if (kk > n) { kk = 2 * n - kk; sgn = -sgn; }
+            if (kk < 0) { kk = -kk; flip = (long long)0x8000000000000000ULL; }
+            else if (kk > n) { kk = 2 * n - kk; flip = (long long)0x8000000000000000ULL; }
             k[d] = kk;
         } else {
             k[d] = cell_map(k[d], G.n[d], G.bc[d]);
@@ -111,7 +124,7 @@ __device__ __forceinline__ double load_normal(const Grid& G, const double* __res
     }
     double v = __ldg(u + flat(G, k[0], k[1], k[2]));
     // sign flip on the sign bit (integer pipe) instead of an FP64 multiply
-    return sgn < 0.0 ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL) : v;
+    return __longlong_as_double(__double_as_longlong(v) ^ flip);
 }
 
 // True when slot p is the wall face of direction c.
@@ -125,23 +138,71 @@ __device__ __forceinline__ double vanleer(double a, double b) {
     return ab > 0.0 ? (2.0 * ab) / (a + b) : 0.0;
 }
 
+// Sign tests on the bit pattern (integer pipe; the flux kernels are bound by
+// the FP64 pipe).  For every non-NaN x: nonneg(x) == (x >= 0.0) (both zeros
+// count), positive(x) == (x > 0.0).
+__device__ __forceinline__ bool nonneg(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) == 0ull || (b << 1) == 0ull;
+}
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+
 // Upwind reconstruction without divergent branches.  With q_near the cell
 // on the upwind side of the face, q_far its other neighbour and q_other the
 // cell across the face, the face value is
 //     q_near + s/2,   s = vanleer(q_near - q_far, q_other - q_near).
 // For the right-hand (negative speed) case this is q_R - s_R/2 exactly,
 // because the two differences change sign, which is exact, and s/2 =
-// ab/(a+b) exactly (scaling by two commutes with rounding).  The division
-// is executed by every thread (denominator 1 where the limiter is off) so
-// the warp does not split.
-__device__ __forceinline__ double upwind_value(double q_near, double q_far, double q_other) {
-    double a = q_near - q_far;
-    double b = q_other - q_near;
-    double ab = a * b;
-    bool pos = ab > 0.0;
-    double den = pos ? (a + b) : 1.0;
-    double half_s = ab / den;
-    return q_near + (pos ? half_s : 0.0);
+// ab/(a+b) exactly (scaling by two commutes with rounding).  The value is
+// returned split as q + num/den: num = ab and den = a + b where the limiter
+// is on, num = 0 and den = 1 where it is off, so every thread divides (no
+// warp split) and a thread can form all its reciprocals together.
+struct Upw { double q, num, den; };
+__device__ __forceinline__ Upw upwind_parts(double q_near, double q_far, double q_other) {
+    const double a = q_near - q_far;
+    const double b = q_other - q_near;
+    const double ab = a * b;
+    const bool on = positive(ab);
+    Upw u;
+    u.q = q_near;
+    u.num = on ? ab : 0.0;
+    u.den = on ? a + b : 1.0;
+    return u;
+}
+
+// r[i] = 1/d[i], i < K, with one division: Montgomery's simultaneous
+// inversion (P. L. Montgomery, Math. Comp. 48 (1987) 243-264):
+// prefix products p_i = d_0 ... d_i, one reciprocal 1/p_{K-1}, then going
+// down r_i = p_{i-1} / p_i and 1/p_{i-1} = d_i / p_i.  It costs 3(K-1)
+// multiplications instead of K-1 divisions; each result carries at most 3K
+// roundings instead of one.  The prefix products stay in the normal range
+// when every |d_i| lies in [2^-R, 2^R), R = 1000/K (exponent test on the high
+// word, integer pipe); otherwise the thread divides K times.
+template <int K>
+__device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K]) {
+    constexpr unsigned R = 1000u / K;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const unsigned e = ((unsigned)__double2hiint(d[i]) >> 20) & 0x7ffu;
+        ok = ok & (e - (1023u - R) < 2u * R);
+    }
+    if (ok) {
+        double p[K];
+        p[0] = d[0];
+#pragma unroll
+        for (int i = 1; i < K; ++i) p[i] = p[i - 1] * d[i];
+        double inv = 1.0 / p[K - 1];
+#pragma unroll
+        for (int i = K - 1; i > 0; --i) {
+            r[i] = inv * p[i - 1];
+            inv = inv * d[i];
+        }
+        r[0] = inv;
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) r[i] = 1.0 / d[i];
+    }
 }
 
 template <typename T> struct Acc { typedef double type; };

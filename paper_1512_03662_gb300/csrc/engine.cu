@@ -41,6 +41,7 @@ struct jfnk_handle {
     // temporaries, right-hand side, multiplier and a scaled input vector
     double *adj, *Xb, *rub, *reb, *rpb, *b64, *lam, *w64;
     long long npartials;
+    long long ldv;     // column stride of V and Z: nvec rounded up to 64 (16-byte aligned columns)
     std::vector<MGLevel> levels;
     size_t elt;        // bytes per basis element
 };
@@ -93,7 +94,7 @@ size_t plan(jfnk_handle* h, char* base) {
     h->FE = (double*)take(nd * nc * 8);
     h->Psi = (double*)take((long long)nd * nd * nc * 8);
     long long cb = cell_blocks(h->G);
-    h->npartials = std::max<long long>(cb, (long long)kRedBlocks * (m + 1));
+    h->npartials = std::max<long long>(cb, (long long)std::max(kRedBlocks, kMaxRedBlocks) * (m + 1));
     h->partials = (double*)take(h->npartials * 8);
     h->scal = (double*)take(kNumSlots * 8);
     h->H = (double*)take((size_t)(m + 1) * m * 8);
@@ -112,8 +113,8 @@ size_t plan(jfnk_handle* h, char* base) {
     h->lam = (double*)take(nv * 8);
     h->w64 = (double*)take(nv * 8);
     const size_t e = h->elt;
-    h->V = take((size_t)(m + 1) * nv * e);
-    h->Z = take((size_t)m * nv * e);
+    h->V = take((size_t)(m + 1) * h->ldv * e);
+    h->Z = take((size_t)m * h->ldv * e);
     if (h->nf > 0) {
         h->rp = take(nc * e);
         h->re = take(nc * e);
@@ -188,9 +189,9 @@ void scaling(jfnk_handle* h, const double* X) {
 }
 
 template <typename T>
-T* Vcol(jfnk_handle* h, int j) { return (T*)h->V + (long long)j * h->nvec; }
+T* Vcol(jfnk_handle* h, int j) { return (T*)h->V + (long long)j * h->ldv; }
 template <typename T>
-T* Zcol(jfnk_handle* h, int j) { return (T*)h->Z + (long long)j * h->nvec; }
+T* Zcol(jfnk_handle* h, int j) { return (T*)h->Z + (long long)j * h->ldv; }
 
 // coefficients of the preconditioner at X (needs the scaling of X)
 void si_setup(jfnk_handle* h, const double* X, double dt) {
@@ -205,7 +206,10 @@ void si_setup(jfnk_handle* h, const double* X, double dt) {
 
 // one V-cycle from level l; tr = 1 solves the transposed system
 template <typename T>
-void vcycle(jfnk_handle* h, size_t l, int tr = 0) {
+// x_l starts at zero on coarse levels and, in the first cycle, on level 0
+// (zero_start: the first half sweep reads no neighbours; the other colour is
+// overwritten before it is read)
+void vcycle(jfnk_handle* h, size_t l, int tr = 0, bool first = false) {
     cudaStream_t s = h->stream;
     auto& Lv = h->levels;
     if (l + 1 == Lv.size()) {
@@ -213,10 +217,10 @@ void vcycle(jfnk_handle* h, size_t l, int tr = 0) {
         return;
     }
     for (int k = 0; k < h->opt.mg_nu1; ++k) {
-        launch_smooth<T>(h->G, h->nf, Lv[l], 0, s, tr);
+        launch_smooth<T>(h->G, h->nf, Lv[l], 0, s, tr, (k == 0 && (l > 0 || first)) ? 1 : 0);
         launch_smooth<T>(h->G, h->nf, Lv[l], 1, s, tr);
     }
-    launch_restrict<T>(h->G, h->nf, Lv[l], Lv[l + 1], s, tr);
+    launch_restrict<T>(h->G, h->nf, Lv[l], Lv[l + 1], s, tr, h->opt.mg_nu1 > 0 ? 1 : 0);
     vcycle<T>(h, l + 1, tr);
     launch_prolong<T>(h->G, h->nf, Lv[l], Lv[l + 1], s);
     for (int k = 0; k < h->opt.mg_nu2; ++k) {
@@ -238,8 +242,8 @@ void precond(jfnk_handle* h, const double* X, double dt, const T* v, int vslot, 
     }
     (void)X;
     launch_precond_in<T>(h->G, (const T*)h->C, v, h->vscale, vslot, h->nf, (T*)h->rp, (T*)h->re, (T*)h->ru,
-                         h->levels[0], s);
-    for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<T>(h, 0);
+                         h->levels[0], s, h->opt.mg_nu1 > 0 ? 0 : 1);
+    for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<T>(h, 0, 0, c == 0);
     launch_precond_out<T>(h->G, (const T*)h->C, dt, h->nf, (const T*)h->rp, (const T*)h->re, (const T*)h->ru,
                           h->levels[0], z, h->partials, s);
     launch_finalize(h->partials, (int)cblocks(h), h->scal, kSlotZnorm, 0, s);
@@ -342,17 +346,19 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
             {
                 Timer t(h, 8);
                 double* hcol = h->H + (long long)j * ldh;
-                launch_multidot<T>(Vcol<T>(h, 0), n, j + 1, Vcol<T>(h, j + 1), n, h->partials, s);
-                launch_multidot_finalize(h->partials, kRedBlocks, j + 1, h->vscale, hcol, 0, s);
-                launch_axpy_norm<T>(Vcol<T>(h, j + 1), Vcol<T>(h, 0), n, j + 1, hcol, h->vscale, n, h->partials, s);
+                const long long ld = h->ldv;
+                int nb = launch_multidot<T>(Vcol<T>(h, 0), ld, j + 1, Vcol<T>(h, j + 1), n, h->partials, s);
+                launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, hcol, 0, s);
+                nb = launch_axpy_norm<T>(Vcol<T>(h, j + 1), Vcol<T>(h, 0), ld, j + 1, hcol, h->vscale, n, h->partials,
+                                         s);
                 if (h->opt.reorth) {
-                    launch_multidot<T>(Vcol<T>(h, 0), n, j + 1, Vcol<T>(h, j + 1), n, h->partials, s);
-                    launch_multidot_finalize(h->partials, kRedBlocks, j + 1, h->vscale, h->hc2, 0, s);
-                    launch_axpy_norm<T>(Vcol<T>(h, j + 1), Vcol<T>(h, 0), n, j + 1, h->hc2, h->vscale, n, h->partials,
-                                        s);
+                    nb = launch_multidot<T>(Vcol<T>(h, 0), ld, j + 1, Vcol<T>(h, j + 1), n, h->partials, s);
+                    launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, h->hc2, 0, s);
+                    nb = launch_axpy_norm<T>(Vcol<T>(h, j + 1), Vcol<T>(h, 0), ld, j + 1, h->hc2, h->vscale, n,
+                                             h->partials, s);
                     launch_add_col(hcol, h->hc2, j + 1, s);
                 }
-                launch_finalize(h->partials, kRedBlocks, h->scal, kSlotTmp, 0, s);
+                launch_finalize(h->partials, nb, h->scal, kSlotTmp, 0, s);
                 launch_set_subdiag(h->scal, hcol, j, h->vscale, s);
                 launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
                 t.stop();
@@ -377,7 +383,7 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
         }
         if (k > 0) {
             launch_backsolve(h->H, ldh, k, h->g, h->y, s);
-            launch_update<T>(h->dxh, (const T*)h->Z, n, k, h->y, n, s);
+            launch_update<T>(h->dxh, (const T*)h->Z, h->ldv, k, h->y, n, s);
         }
         so.iterations = total;
         so.res = res / beta0;
@@ -428,7 +434,7 @@ void precond_T(jfnk_handle* h, double dt, const double* y, double* z) {
         return;
     }
     launch_precondT_out(h->G, (const double*)h->C, dt, h->nf, y, h->rub, h->reb, h->rpb, h->levels[0], s);
-    for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<double>(h, 0, 1);
+    for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<double>(h, 0, 1, c == 0);
     launch_precondT_in(h->G, (const double*)h->C, h->nf, h->levels[0], h->rub, h->reb, h->rpb, z, s);
 }
 
@@ -468,23 +474,24 @@ jfnk_status gmres_adj(jfnk_handle* h, const double* X, double dt, double eta, So
         bool done = false;
         for (int j = 0; j < m; ++j) {
             if (total >= h->opt.gmres_max_it) break;
-            double* Vj = V + (long long)j * n;
-            double* Zj = Z + (long long)j * n;
-            double* Vn = V + (long long)(j + 1) * n;
+            const long long ld = h->ldv;
+            double* Vj = V + (long long)j * ld;
+            double* Zj = Z + (long long)j * ld;
+            double* Vn = V + (long long)(j + 1) * ld;
             launch_scale_copy<double, double>(Vj, 1.0, h->vscale, j, 0, h->w64, n, s);
             precond_T(h, dt, h->w64, Zj);
             jT_apply(h, X, dt, Zj, Vn);
             double* hcol = h->H + (long long)j * ldh;
-            launch_multidot<double>(V, n, j + 1, Vn, n, h->partials, s);
-            launch_multidot_finalize(h->partials, kRedBlocks, j + 1, h->vscale, hcol, 0, s);
-            launch_axpy_norm<double>(Vn, V, n, j + 1, hcol, h->vscale, n, h->partials, s);
+            int nb = launch_multidot<double>(V, ld, j + 1, Vn, n, h->partials, s);
+            launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, hcol, 0, s);
+            nb = launch_axpy_norm<double>(Vn, V, ld, j + 1, hcol, h->vscale, n, h->partials, s);
             if (h->opt.reorth) {
-                launch_multidot<double>(V, n, j + 1, Vn, n, h->partials, s);
-                launch_multidot_finalize(h->partials, kRedBlocks, j + 1, h->vscale, h->hc2, 0, s);
-                launch_axpy_norm<double>(Vn, V, n, j + 1, h->hc2, h->vscale, n, h->partials, s);
+                nb = launch_multidot<double>(V, ld, j + 1, Vn, n, h->partials, s);
+                launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, h->hc2, 0, s);
+                nb = launch_axpy_norm<double>(Vn, V, ld, j + 1, h->hc2, h->vscale, n, h->partials, s);
                 launch_add_col(hcol, h->hc2, j + 1, s);
             }
-            launch_finalize(h->partials, kRedBlocks, h->scal, kSlotTmp, 0, s);
+            launch_finalize(h->partials, nb, h->scal, kSlotTmp, 0, s);
             launch_set_subdiag(h->scal, hcol, j, h->vscale, s);
             launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
             if ((st = sync_read(h)) != JFNK_OK) return st;
@@ -501,7 +508,7 @@ jfnk_status gmres_adj(jfnk_handle* h, const double* X, double dt, double eta, So
         }
         if (k > 0) {
             launch_backsolve(h->H, ldh, k, h->g, h->y, s);
-            launch_update<double>(h->dxh, Z, n, k, h->y, n, s);
+            launch_update<double>(h->dxh, Z, h->ldv, k, h->y, n, s);
         }
         so.iterations = total;
         so.res = res / beta0;
@@ -606,8 +613,10 @@ jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_g
     G.chi_exp = cond ? cond->exponent : 3.0;
     if (G.K0 < 0.0) { *out = h; return fail(h, JFNK_EINVAL, "K0 must be >= 0"); }
     G.theta = h->opt.theta;
+    set_grid_flags(G);
     h->nc = G.ncell;
     h->nvec = (2 + G.ndim) * G.ncell;
+    h->ldv = (h->nvec + 63) / 64 * 64;
     h->nf = h->opt.precond == JFNK_PRECOND_SOUND ? 1 : (h->opt.precond == JFNK_PRECOND_SOUND_DIFF ? 2 : 0);
     h->mixed = h->opt.precision == JFNK_MIXED;
     h->elt = h->mixed ? sizeof(float) : sizeof(double);

@@ -54,13 +54,15 @@ void launch_norm2_partials(const T* x, long long n, double* partials, cudaStream
 template <typename T>
 void launch_dot_partials(const double* a, const double* ainv_scale, const T* b, long long n, double* partials,
                          cudaStream_t s);
+// multi-dot and AXPY + norm return the number of blocks (partial sums per
+// vector) of their occupancy-sized grid, at most kMaxRedBlocks
 template <typename T>
-void launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s);
+int launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s);
 void launch_multidot_finalize(const double* partials, int nblocks, int nv, const double* vscale, double* hcol,
                               int accumulate, cudaStream_t s);
 template <typename T>
-void launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
-                      double* partials, cudaStream_t s);
+int launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
+                     double* partials, cudaStream_t s);
 // hcol[j+1] = norm, vscale[j+1] = 1/norm
 void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s);
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* scal, cudaStream_t s);
@@ -109,14 +111,20 @@ void launch_pc_setup(const Grid& G, const double* X, const double* L, const doub
                      MGLevel& L0, cudaStream_t s);
 template <typename T>
 void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStream_t s);
+// zero_x = 1: also zero the level-0 multigrid unknowns (needed when the
+// V-cycle does not start with a zero-start half sweep)
 template <typename T>
 void launch_precond_in(const Grid& G, const T* C, const T* v, const double* vscale, int vslot, int nf, T* rp, T* re,
-                       T* ru, MGLevel& L0, cudaStream_t s);
-// tr = 1: the transposed multigrid system (cell matrices transposed)
+                       T* ru, MGLevel& L0, cudaStream_t s, int zero_x);
+// tr = 1: the transposed multigrid system (cell matrices transposed);
+// zero_start = 1: x is zero on entry (no neighbour loads)
 template <typename T>
-void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr = 0);
+void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr = 0, int zero_start = 0);
+// red_only = 1 after at least one pre-smoothing sweep (the last half sweep
+// leaves a zero residual on colour-1 cells): residual and restriction read
+// colour-0 cells only
 template <typename T>
-void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr = 0);
+void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr = 0, int red_only = 0);
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
 template <typename T>

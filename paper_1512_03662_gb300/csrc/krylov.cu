@@ -38,6 +38,27 @@ __device__ __forceinline__ void comp_fma(CompF& a, float x, float y) {
     a.e = __fadd_rn(a.e, err);
 }
 
+// Grid of a grid-stride reduction: as many blocks as are resident on all
+// SMs at once (one wave: no tail wave, every SM equally loaded), capped at
+// kMaxRedBlocks.  Fixed per kernel and device, so the summation order and
+// the results stay reproducible.
+static int red_grid(const void* fn) {
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0);
+    long long g = (long long)(nsm > 0 ? nsm : 1) * (occ > 0 ? occ : 1);
+    return (int)(g < kMaxRedBlocks ? g : kMaxRedBlocks);
+}
+
+// one cached grid per kernel (the kernel is the template argument, so each
+// instantiation has its own thread-safe static)
+template <auto FN>
+static int cached_grid() {
+    static const int g = red_grid((const void*)FN);
+    return g;
+}
+
 __global__ void k_finalize(const double* __restrict__ partials, int n, double* scal, int slot, int op) {
     __shared__ double sh[32];
     double v = (op == 2) ? 0.0 : 0.0;
@@ -154,6 +175,46 @@ __global__ void k_multidot_f32(const float* __restrict__ V, long long ld, const 
     }
 }
 
+// The same with 16-byte loads: each thread takes four consecutive elements
+// per step, which keeps enough bytes in flight per SM to cover HBM latency
+// when the basis is short (one load instruction per vector per four
+// elements).  Needs ld % 4 == 0 and 16-byte aligned V and w; the n % 4 tail
+// is summed element by element.
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_multidot_f32v(const float* __restrict__ V, long long ld,
+                                                          const float* __restrict__ w, long long n,
+                                                          double* __restrict__ partials) {
+    __shared__ double sh[32];
+    CompF acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = CompF{0.f, 0.f};
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = n >> 2;
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    for (long long k = t0; k < n4; k += stride) {
+        const float4 wk = w4[k];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(V + i * ld)[k];
+            comp_fma(acc[i], v.x, wk.x);
+            comp_fma(acc[i], v.y, wk.y);
+            comp_fma(acc[i], v.z, wk.z);
+            comp_fma(acc[i], v.w, wk.w);
+        }
+    }
+    for (long long k = 4 * n4 + t0; k < n; k += stride) {
+        const float wk = w[k];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) comp_fma(acc[i], V[i * ld + k], wk);
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = block_sum<kBlock>((double)acc[i].s + (double)acc[i].e, sh);
+        if (threadIdx.x == 0) partials[blockIdx.x * NV + i] = s;
+    }
+}
+
 // generic fallback for any count: loops over groups of 8
 template <typename T>
 __global__ void k_multidot_group(const T* __restrict__ V, long long ld, int i0, int ni, int nvtot,
@@ -174,14 +235,27 @@ __global__ void k_multidot_group(const T* __restrict__ V, long long ld, int i0, 
     }
 }
 
+static inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 template <typename T>
-void launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s) {
+int launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, double* partials, cudaStream_t s) {
     if (sizeof(T) == 4 && nv <= 32) {
         const float* Vf = (const float*)V;
         const float* wf = (const float*)w;
+        const bool vec = ld % 4 == 0 && aligned16(V) && aligned16(w);
+        int g = 0;
         ++g_launch_count;
         switch (nv) {
-#define CASEF(N) case N: k_multidot_f32<N><<<kRedBlocks, kBlock, 0, s>>>(Vf, ld, wf, n, partials); return;
+#define CASEF(N)                                                                                   \
+    case N:                                                                                        \
+        if (vec) {                                                                                 \
+            g = cached_grid<k_multidot_f32v<N>>();                                                 \
+            k_multidot_f32v<N><<<g, kBlock, 0, s>>>(Vf, ld, wf, n, partials);                       \
+        } else {                                                                                   \
+            g = cached_grid<k_multidot_f32<N>>();                                                  \
+            k_multidot_f32<N><<<g, kBlock, 0, s>>>(Vf, ld, wf, n, partials);                        \
+        }                                                                                          \
+        return g;
             CASEF(1) CASEF(2) CASEF(3) CASEF(4) CASEF(5) CASEF(6) CASEF(7) CASEF(8)
             CASEF(9) CASEF(10) CASEF(11) CASEF(12) CASEF(13) CASEF(14) CASEF(15) CASEF(16)
             CASEF(17) CASEF(18) CASEF(19) CASEF(20) CASEF(21) CASEF(22) CASEF(23) CASEF(24)
@@ -189,21 +263,29 @@ void launch_multidot(const T* V, long long ld, int nv, const T* w, long long n, 
 #undef CASEF
         }
     }
+    int g = 0;
     switch (nv) {
-#define CASE(N) case N: ++g_launch_count; k_multidot<T, N><<<kRedBlocks, kBlock, 0, s>>>(V, ld, w, n, partials); return;
+#define CASE(N)                                                                                    \
+    case N:                                                                                        \
+        ++g_launch_count;                                                                          \
+        g = cached_grid<k_multidot<T, N>>();                                                       \
+        k_multidot<T, N><<<g, kBlock, 0, s>>>(V, ld, w, n, partials);                               \
+        return g;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
         CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
 #undef CASE
         default:
+            g = cached_grid<k_multidot_group<T>>();
             for (int i0 = 0; i0 < nv; i0 += 8) {
                 int ni = nv - i0 < 8 ? nv - i0 : 8;
                 ++g_launch_count;
-                k_multidot_group<T><<<kRedBlocks, kBlock, 0, s>>>(V, ld, i0, ni, nv, w, n, partials);
+                k_multidot_group<T><<<g, kBlock, 0, s>>>(V, ld, i0, ni, nv, w, n, partials);
             }
+            return g;
     }
 }
-template void launch_multidot<double>(const double*, long long, int, const double*, long long, double*, cudaStream_t);
-template void launch_multidot<float>(const float*, long long, int, const float*, long long, double*, cudaStream_t);
+template int launch_multidot<double>(const double*, long long, int, const double*, long long, double*, cudaStream_t);
+template int launch_multidot<float>(const float*, long long, int, const float*, long long, double*, cudaStream_t);
 
 // hcol[i] (+)= vscale[i] * sum_b partials[b * nv + i]; one block per i
 __global__ void k_multidot_finalize(const double* __restrict__ partials, int nblocks, int nv,
@@ -300,15 +382,90 @@ __global__ void k_axpy_norm_f32(float* __restrict__ w, const float* __restrict__
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The same with 16-byte loads and stores (four consecutive elements per
+// thread and step); needs ld % 4 == 0 and 16-byte aligned w and V.
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_axpy_norm_f32v(float* __restrict__ w, const float* __restrict__ V,
+                                                           long long ld, const double* __restrict__ hcol,
+                                                           const double* __restrict__ vscale, long long n,
+                                                           double* __restrict__ partials) {
+    __shared__ double sh[32];
+    __shared__ float chi[32], clo[32];
+    if (threadIdx.x < NV) {
+        double c = -(hcol[threadIdx.x] * vscale[threadIdx.x]);
+        float h = (float)c;
+        chi[threadIdx.x] = h;
+        clo[threadIdx.x] = (float)(c - (double)h);
+    }
+    __syncthreads();
+    CompF nrm{0.f, 0.f};
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = n >> 2;
+    float4* w4 = reinterpret_cast<float4*>(w);
+    for (long long k = t0; k < n4; k += stride) {
+        const float4 wk = w4[k];
+        CompF x0{wk.x, 0.f}, x1{wk.y, 0.f}, x2{wk.z, 0.f}, x3{wk.w, 0.f};
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(V + i * ld)[k];
+            const float ch = chi[i], cl = clo[i];
+            comp_fma(x0, ch, v.x);
+            x0.e = fmaf(cl, v.x, x0.e);
+            comp_fma(x1, ch, v.y);
+            x1.e = fmaf(cl, v.y, x1.e);
+            comp_fma(x2, ch, v.z);
+            x2.e = fmaf(cl, v.z, x2.e);
+            comp_fma(x3, ch, v.w);
+            x3.e = fmaf(cl, v.w, x3.e);
+        }
+        float4 o;
+        o.x = x0.s + x0.e;
+        o.y = x1.s + x1.e;
+        o.z = x2.s + x2.e;
+        o.w = x3.s + x3.e;
+        w4[k] = o;
+        comp_fma(nrm, o.x, o.x);
+        comp_fma(nrm, o.y, o.y);
+        comp_fma(nrm, o.z, o.z);
+        comp_fma(nrm, o.w, o.w);
+    }
+    for (long long k = 4 * n4 + t0; k < n; k += stride) {
+        CompF x{w[k], 0.f};
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            float v = V[i * ld + k];
+            comp_fma(x, chi[i], v);
+            x.e = fmaf(clo[i], v, x.e);
+        }
+        float xs = x.s + x.e;
+        w[k] = xs;
+        comp_fma(nrm, xs, xs);
+    }
+    double sum = block_sum<kBlock>((double)nrm.s + (double)nrm.e, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
 template <typename T>
-void launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
-                      double* partials, cudaStream_t s) {
+int launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
+                     double* partials, cudaStream_t s) {
     if (sizeof(T) == 4 && nv <= 32) {
         float* wf = (float*)w;
         const float* Vf = (const float*)V;
+        const bool vec = ld % 4 == 0 && aligned16(V) && aligned16(w);
+        int g = 0;
         ++g_launch_count;
         switch (nv) {
-#define CASEF(N) case N: k_axpy_norm_f32<N><<<kRedBlocks, kBlock, 0, s>>>(wf, Vf, ld, hcol, vscale, n, partials); return;
+#define CASEF(N)                                                                                   \
+    case N:                                                                                        \
+        if (vec) {                                                                                 \
+            g = cached_grid<k_axpy_norm_f32v<N>>();                                                \
+            k_axpy_norm_f32v<N><<<g, kBlock, 0, s>>>(wf, Vf, ld, hcol, vscale, n, partials);        \
+        } else {                                                                                   \
+            g = cached_grid<k_axpy_norm_f32<N>>();                                                 \
+            k_axpy_norm_f32<N><<<g, kBlock, 0, s>>>(wf, Vf, ld, hcol, vscale, n, partials);         \
+        }                                                                                          \
+        return g;
             CASEF(1) CASEF(2) CASEF(3) CASEF(4) CASEF(5) CASEF(6) CASEF(7) CASEF(8)
             CASEF(9) CASEF(10) CASEF(11) CASEF(12) CASEF(13) CASEF(14) CASEF(15) CASEF(16)
             CASEF(17) CASEF(18) CASEF(19) CASEF(20) CASEF(21) CASEF(22) CASEF(23) CASEF(24)
@@ -316,20 +473,28 @@ void launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol
 #undef CASEF
         }
     }
+    int g = 0;
     switch (nv) {
-#define CASE(N) case N: ++g_launch_count; k_axpy_norm<T, N><<<kRedBlocks, kBlock, 0, s>>>(w, V, ld, hcol, vscale, n, partials); return;
+#define CASE(N)                                                                                    \
+    case N:                                                                                        \
+        ++g_launch_count;                                                                          \
+        g = cached_grid<k_axpy_norm<T, N>>();                                                      \
+        k_axpy_norm<T, N><<<g, kBlock, 0, s>>>(w, V, ld, hcol, vscale, n, partials);                \
+        return g;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
         CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
 #undef CASE
         default:
             ++g_launch_count;
-            k_axpy_norm_dyn<T><<<kRedBlocks, kBlock, 0, s>>>(w, V, ld, nv, hcol, vscale, n, partials);
+            g = cached_grid<k_axpy_norm_dyn<T>>();
+            k_axpy_norm_dyn<T><<<g, kBlock, 0, s>>>(w, V, ld, nv, hcol, vscale, n, partials);
+            return g;
     }
 }
-template void launch_axpy_norm<double>(double*, const double*, long long, int, const double*, const double*, long long,
-                                       double*, cudaStream_t);
-template void launch_axpy_norm<float>(float*, const float*, long long, int, const double*, const double*, long long,
+template int launch_axpy_norm<double>(double*, const double*, long long, int, const double*, const double*, long long,
                                       double*, cudaStream_t);
+template int launch_axpy_norm<float>(float*, const float*, long long, int, const double*, const double*, long long,
+                                     double*, cudaStream_t);
 
 __global__ void k_set_subdiag(double* scal, double* hcol, int j, double* vscale) {
     double nrm = scal[kSlotTmp];

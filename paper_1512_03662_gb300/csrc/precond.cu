@@ -67,7 +67,7 @@ __device__ __forceinline__ long long mg0(const Grid& G, const Idx3& P) {
 __device__ __forceinline__ int wrapi(int k, int n) { return k < 0 ? k + n : (k >= n ? k - n : k); }
 
 __device__ __forceinline__ double conductivity_si(const Grid& G, double T) {
-    return G.chi_exp == 3.0 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+    return G.chi3 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
 }
 
 // ---------------------------------------------------------------------------
@@ -142,7 +142,7 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
         M[3 * nc + mi] = (T)(B.b11 / dt);
     }
     const double cv = 1.0 / G.gm1;
-    const double chi0 = (G.K0 != 0.0) ? conductivity_si(G, G.gm1 * e) : 0.0;
+    const double chi0 = (G.has_cond) ? conductivity_si(G, G.gm1 * e) : 0.0;
     double dpdrho = G.gm1 * e, dpde = G.gm1 * rho;
     C[PcLr * nc + cc] = (T)L[cc];
     C[PcLE * nc + cc] = (T)L[nc + cc];
@@ -183,15 +183,15 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
 #pragma unroll
     for (int c = 0; c < ND; ++c) {
         const bool wall = is_wall_slot(G, c, P);
-        double m = (wall || G.n[c] == 1) ? 0.0 : 1.0;
         int o[3] = {0, 0, 0};
         o[c] = -1;
         double rl = load_cell(G, X, P, o[0], o[1], o[2]);
         double rho_f = 0.5 * (rl + rho);
+        const double m = (wall || G.n[c] == 1) ? 0.0 : 1.0;
         K[(0 * ND + c) * nc + mi] = (T)(m / rho_f);
         if (nf == 2) {
             double chil = 0.0;
-            if (G.K0 != 0.0) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
+            if (G.has_cond) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
             K[(1 * ND + c) * nc + mi] = (T)(m * (0.5 * (chil + chi0)) / cv);
         }
         const double u = wall ? 0.0 : X[(2 + c) * nc + cc];
@@ -328,7 +328,8 @@ __device__ __forceinline__ T ru_at(const Grid& G, const T* C, const TV* v, T s, 
 template <int ND, typename T>
 __global__ void k_precond_in(Grid G, const T* __restrict__ C, const T* __restrict__ v,
                              const double* __restrict__ vscale, int vslot, int nf, T* __restrict__ rp,
-                             T* __restrict__ re, T* __restrict__ ru, T* __restrict__ rhs, T* __restrict__ x0) {
+                             T* __restrict__ re, T* __restrict__ ru, T* __restrict__ rhs, T* __restrict__ x0,
+                             int zero_x) {
     Idx3 P;
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
@@ -359,13 +360,14 @@ __global__ void k_precond_in(Grid G, const T* __restrict__ C, const T* __restric
     }
 #pragma unroll
     for (int c = 0; c < ND; ++c) ru[c * nc + cc] = ruv[c];
-    re[cc] = r_e;
+    // r_p and r_e are kept for the back substitution of the sound-only scheme
+    if (nf == 1) re[cc] = r_e;
     const long long mi = mg0(G, P);
     if (sizeof(T) == 8) {
         // double: the oracle's order, r_p = dp/drho r_rho + dp/de r_e, rhs = B^-1 (r_p, r_e)
         T r_p = C[PcDpdrho * nc + cc] * r_rho + C[PcDpde * nc + cc] * r_e;
-        rp[cc] = r_p;
         if (nf == 1) {
+            rp[cc] = r_p;
             rhs[mi] = r_p * C[PcQ0 * nc + cc];
         } else {
             rhs[mi] = C[PcQ0 * nc + cc] * r_p + C[PcQ1 * nc + cc] * r_e;
@@ -373,25 +375,27 @@ __global__ void k_precond_in(Grid G, const T* __restrict__ C, const T* __restric
         }
     } else {
         // float: folded coefficients (see PcQ*), free of cancellation
-        T r_p = C[PcPr * nc + cc] * r_rho + C[PcPE * nc + cc] * r_E - C[PcDpde * nc + cc] * dot_ur;
-        rp[cc] = r_p;
+        if (nf == 1) rp[cc] = C[PcPr * nc + cc] * r_rho + C[PcPE * nc + cc] * r_E - C[PcDpde * nc + cc] * dot_ur;
         rhs[mi] = C[PcQ0 * nc + cc] * r_rho + C[PcQ1 * nc + cc] * r_E - C[PcQ2 * nc + cc] * dot_ur;
         if (nf == 2)
             rhs[nc + mi] = C[PcQ3 * nc + cc] * r_rho + C[PcQ4 * nc + cc] * r_E - C[PcQ5 * nc + cc] * dot_ur;
     }
-    x0[mi] = (T)0;
-    if (nf == 2) x0[nc + mi] = (T)0;
+    // the first half sweep can take a zero start without reading x
+    if (zero_x) {
+        x0[mi] = (T)0;
+        if (nf == 2) x0[nc + mi] = (T)0;
+    }
 }
 
 template <typename T>
 void launch_precond_in(const Grid& G, const T* C, const T* v, const double* vscale, int vslot, int nf, T* rp, T* re,
-                       T* ru, MGLevel& L0, cudaStream_t s) {
-    CELL_LAUNCH_T(k_precond_in, T, G, C, v, vscale, vslot, nf, rp, re, ru, (T*)L0.rhs, (T*)L0.x);
+                       T* ru, MGLevel& L0, cudaStream_t s, int zero_x) {
+    CELL_LAUNCH_T(k_precond_in, T, G, C, v, vscale, vslot, nf, rp, re, ru, (T*)L0.rhs, (T*)L0.x, zero_x);
 }
 template void launch_precond_in<double>(const Grid&, const double*, const double*, const double*, int, int, double*,
-                                        double*, double*, MGLevel&, cudaStream_t);
+                                        double*, double*, MGLevel&, cudaStream_t, int);
 template void launch_precond_in<float>(const Grid&, const float*, const float*, const double*, int, int, float*,
-                                       float*, float*, MGLevel&, cudaStream_t);
+                                       float*, float*, MGLevel&, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // multigrid
@@ -419,8 +423,12 @@ __device__ __forceinline__ void nb_index(const LvlDev& L, int d, int a, int b, i
 // i+j+k).  With an even x extent each thread takes one cell of the colour
 // (compact mapping); otherwise threads of the other colour return.  Loops
 // over directions and fields are unrolled at compile time (ND, NF) so all
-// per-thread arrays stay in registers.
-template <typename T, int NF, int ND>
+// per-thread arrays stay in registers.  ZS: x is zero on entry, so the
+// neighbour values are not read (first half sweep of a level that starts
+// from zero; the cells of the other colour are overwritten before they are
+// read).  A run-time flag in its place cost the kernel 12 registers and a
+// quarter of its occupancy.
+template <typename T, int NF, int ND, bool ZS>
 __global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
                          const T* __restrict__ rhs, int colour, int compact, int tr) {
     const int b = blockIdx.y * blockDim.y + threadIdx.y;
@@ -442,10 +450,12 @@ __global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const T* Kd = K + (long long)(f * ND + d) * Lv.nc;
-            const T* xf = x + (long long)f * Lv.nc;
             T Kl = Kd[cc], Ku = Kd[ju];
             dg[f] = dg[f] + (Kl + Ku) * ih2;
-            of[f] = of[f] + (Ku * xf[ju] + Kl * xf[jd]) * ih2;
+            if (!ZS) {
+                const T* xf = x + (long long)f * Lv.nc;
+                of[f] = of[f] + (Ku * xf[ju] + Kl * xf[jd]) * ih2;
+            }
         }
     }
     if (NF == 1) {
@@ -470,16 +480,28 @@ __global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict
         else KERNEL<T, 2, 2><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);                             \
     } while (0)
 
-template <typename T>
-void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr) {
+template <typename T, bool ZS>
+static void smooth_launch(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr) {
     int compact = (Lv.n[0] % 2 == 0) ? 1 : 0;
     int nx[3] = {compact ? Lv.n[0] / 2 : Lv.n[0], Lv.n[1], Lv.n[2]};
     CellLaunch cl = cell_launch(nx);
-    MG_DISPATCH(k_smooth, cl.grid, cl.block, lvl(Lv), (const T*)Lv.M, (const T*)Lv.K, (T*)Lv.x, (const T*)Lv.rhs,
-                colour, compact, tr);
+    ++g_launch_count;
+    const LvlDev L = lvl(Lv);
+    const T *M = (const T*)Lv.M, *K = (const T*)Lv.K, *rhs = (const T*)Lv.rhs;
+    T* x = (T*)Lv.x;
+    if (nf == 1 && G.ndim == 3) k_smooth<T, 1, 3, ZS><<<cl.grid, cl.block, 0, s>>>(L, M, K, x, rhs, colour, compact, tr);
+    else if (nf == 1) k_smooth<T, 1, 2, ZS><<<cl.grid, cl.block, 0, s>>>(L, M, K, x, rhs, colour, compact, tr);
+    else if (G.ndim == 3) k_smooth<T, 2, 3, ZS><<<cl.grid, cl.block, 0, s>>>(L, M, K, x, rhs, colour, compact, tr);
+    else k_smooth<T, 2, 2, ZS><<<cl.grid, cl.block, 0, s>>>(L, M, K, x, rhs, colour, compact, tr);
 }
-template void launch_smooth<double>(const Grid&, int, MGLevel&, int, cudaStream_t, int);
-template void launch_smooth<float>(const Grid&, int, MGLevel&, int, cudaStream_t, int);
+
+template <typename T>
+void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t s, int tr, int zero_start) {
+    if (zero_start) smooth_launch<T, true>(G, nf, Lv, colour, s, tr);
+    else smooth_launch<T, false>(G, nf, Lv, colour, s, tr);
+}
+template void launch_smooth<double>(const Grid&, int, MGLevel&, int, cudaStream_t, int, int);
+template void launch_smooth<float>(const Grid&, int, MGLevel&, int, cudaStream_t, int, int);
 
 // residual rhs - A x at fine cell (a,b,c), field f
 template <typename T, int NF, int ND>
@@ -503,22 +525,29 @@ __device__ __forceinline__ T fine_residual(const LvlDev& F, const T* M, const T*
     return rhs[(long long)f * F.nc + cc] - out;
 }
 
-// fine residual r = rhs - A x, one thread per fine cell
+// fine residual r = rhs - A x: one thread per fine cell, or (red_only) per
+// colour-0 cell with the compact mapping of the smoother
 template <typename T, int NF, int ND>
 __global__ void k_residual_mg(LvlDev F, const T* __restrict__ M, const T* __restrict__ K, const T* __restrict__ x,
-                             const T* __restrict__ rhs, T* __restrict__ r, int tr) {
-    int i[3];
-    long long cc;
-    if (!lvl_pos(F, i, cc)) return;
+                             const T* __restrict__ rhs, T* __restrict__ r, int tr, int red_only, int compact) {
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    const int c = blockIdx.z;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = compact ? 2 * t + ((b + c) & 1) : t;
+    if (a >= F.n[0] || b >= F.n[1]) return;
+    if (red_only && ((a + b + c) & 1)) return;
+    const long long cc = lflat(F, a, b, c);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-        r[(long long)f * F.nc + cc] = fine_residual<T, NF, ND>(F, M, K, x, rhs, f, i[0], i[1], i[2], tr);
+        r[(long long)f * F.nc + cc] = fine_residual<T, NF, ND>(F, M, K, x, rhs, f, a, b, c, tr);
 }
 
 // coarse right-hand side = mean of the children's residuals (pairs along x,
-// then y, then z); the coarse correction starts from zero
+// then y, then z; colour-1 children count as zero when red_only); the coarse
+// correction starts from zero
 template <typename T, int NF, int ND>
-__global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __restrict__ rhsc, T* __restrict__ xc) {
+__global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __restrict__ rhsc, T* __restrict__ xc,
+                           int red_only, int zero_xc) {
     int ic[3];
     long long cc;
     if (!lvl_pos(C, ic, cc)) return;
@@ -527,9 +556,12 @@ __global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __res
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const T* q = r + (long long)f * F.nc;
+        auto child = [&](int xx, int yy, int zz) -> T {
+            return (red_only && ((xx + yy + zz) & 1)) ? (T)0 : q[lflat(F, xx, yy, zz)];
+        };
         auto xm = [&](int yy, int zz) -> T {
-            T a = q[lflat(F, x0, yy, zz)];
-            return cx ? (a + q[lflat(F, x0 + 1, yy, zz)]) / (T)2 : a;
+            T a = child(x0, yy, zz);
+            return cx ? (a + child(x0 + 1, yy, zz)) / (T)2 : a;
         };
         auto ym = [&](int zz) -> T {
             T a = xm(y0, zz);
@@ -537,20 +569,25 @@ __global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __res
         };
         T a = ym(z0);
         rhsc[(long long)f * C.nc + cc] = cz ? (a + ym(z0 + 1)) / (T)2 : a;
-        xc[(long long)f * C.nc + cc] = (T)0;
+        if (zero_xc) xc[(long long)f * C.nc + cc] = (T)0;
     }
 }
 
 template <typename T>
-void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr) {
-    CellLaunch fl = cell_launch(F.n);
+void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr, int red_only) {
+    const int compact = (red_only && F.n[0] % 2 == 0) ? 1 : 0;
+    int nx[3] = {compact ? F.n[0] / 2 : F.n[0], F.n[1], F.n[2]};
+    CellLaunch fl = cell_launch(nx);
     MG_DISPATCH(k_residual_mg, fl.grid, fl.block, lvl(F), (const T*)F.M, (const T*)F.K, (const T*)F.x,
-                (const T*)F.rhs, (T*)F.r, tr);
+                (const T*)F.rhs, (T*)F.r, tr, red_only, compact);
     CellLaunch cl = cell_launch(C.n);
-    MG_DISPATCH(k_restrict, cl.grid, cl.block, lvl(F), lvl(C), (const T*)F.r, (T*)C.rhs, (T*)C.x);
+    // after a pre-smoothing sweep the coarse level starts with a zero-start
+    // half sweep, so x needs zeroing only without pre-smoothing
+    MG_DISPATCH(k_restrict, cl.grid, cl.block, lvl(F), lvl(C), (const T*)F.r, (T*)C.rhs, (T*)C.x, red_only,
+                red_only ? 0 : 1);
 }
-template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int);
-template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int);
+template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
+template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 
 // coarse parents of fine index i along a coarsened direction
 __device__ __forceinline__ void parents(int i, int nc, int bc, int& par, int& oth) {

@@ -61,7 +61,7 @@ __global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__
 }
 
 __device__ __forceinline__ double conductivity(const Grid& G, double T) {
-    return G.chi_exp == 3.0 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+    return G.chi3 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
 }
 
 template <int ND>
@@ -74,25 +74,39 @@ __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double
     const double* rho = X;
     const double* E = X + nc;
     const double r0 = __ldg(rho + c), e0 = __ldg(E + c);
+    // pass 1: loads and the split upwind values of rho and E on every face
+    double u[ND];
+    Upw up[2 * ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         int o[3] = {0, 0, 0};
-        const double u = load_normal(G, X + (2 + d) * nc, d, P, 0, 0, 0);
+        u[d] = load_normal(G, X + (2 + d) * nc, d, P, 0, 0, 0);
         o[d] = -2; const double r2 = load_cell(G, rho, P, o[0], o[1], o[2]), e2 = load_cell(G, E, P, o[0], o[1], o[2]);
         o[d] = -1; const double r1 = load_cell(G, rho, P, o[0], o[1], o[2]), e1 = load_cell(G, E, P, o[0], o[1], o[2]);
         o[d] = 1;  const double r3 = load_cell(G, rho, P, o[0], o[1], o[2]), e3 = load_cell(G, E, P, o[0], o[1], o[2]);
         // upwind side: cell i-1 for u >= 0 (ties to the lower side), else cell i
-        const bool left = u >= 0.0;
-        const double rho_up = upwind_value(left ? r1 : r0, left ? r2 : r3, left ? r0 : r1);
-        const double E_up = upwind_value(left ? e1 : e0, left ? e2 : e3, left ? e0 : e1);
-        double fm = u * rho_up;
+        const bool left = nonneg(u[d]);
+        up[2 * d] = upwind_parts(left ? r1 : r0, left ? r2 : r3, left ? r0 : r1);
+        up[2 * d + 1] = upwind_parts(left ? e1 : e0, left ? e2 : e3, left ? e0 : e1);
+    }
+    // pass 2: one division for all limited slopes of the cell
+    double den[2 * ND], inv[2 * ND];
+#pragma unroll
+    for (int k = 0; k < 2 * ND; ++k) den[k] = up[k].den;
+    recip_all<2 * ND>(den, inv);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        int o[3] = {0, 0, 0};
+        const double rho_up = up[2 * d].q + up[2 * d].num * inv[2 * d];
+        const double E_up = up[2 * d + 1].q + up[2 * d + 1].num * inv[2 * d + 1];
+        double fm = u[d] * rho_up;
         double fe = fm * E_up;
         o[d] = -1;
         if (G.energy_form == 1) {
             double pl = load_cell(G, p, P, o[0], o[1], o[2]);
-            fe = fe + 0.5 * (pl + __ldg(p + c)) * u;
+            fe = fe + 0.5 * (pl + __ldg(p + c)) * u[d];
         }
-        if (G.K0 != 0.0) {
+        if (G.has_cond) {
             double Tl = load_cell(G, T, P, o[0], o[1], o[2]);
             double Tc = __ldg(T + c);
             double q = 0.5 * (conductivity(G, Tl) + conductivity(G, Tc)) * (Tc - Tl) * G.idx[d];
@@ -125,6 +139,9 @@ __global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double*
     if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
     constexpr int nd = ND;
+    // pass 1 per component c: loads, carrying mass flux and split upwind value
+    double mf[nd * nd];
+    Upw up[nd * nd];
 #pragma unroll
     for (int c = 0; c < nd; ++c) {
         const double* uc = X + (2 + c) * nc;
@@ -140,7 +157,7 @@ __global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double*
                 const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
                 o[c] = 1;  const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
                 o[c] = 2;  const double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                const bool left = m >= 0.0;
+                const bool left = nonneg(m);
                 q_near = left ? u0 : u1;
                 q_far = left ? um : u2;
                 q_other = left ? u1 : u0;
@@ -153,13 +170,24 @@ __global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double*
                 o[d] = -1; const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
                 const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
                 o[d] = 1;  const double u3 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                const bool left = m >= 0.0;
+                const bool left = nonneg(m);
                 q_near = left ? u1 : u0;
                 q_far = left ? u2 : u3;
                 q_other = left ? u0 : u1;
             }
-            Psi[(c * nd + d) * nc + cc] = m * upwind_value(q_near, q_far, q_other);
+            mf[c * nd + d] = m;
+            up[c * nd + d] = upwind_parts(q_near, q_far, q_other);
         }
+        // pass 2: one division for the nd limited slopes of component c (a
+        // batch of nd keeps the kernel near 56 registers; one batch of nd^2
+        // needed 102 and ran 20 % slower at the lower occupancy)
+        double den[nd], inv[nd];
+#pragma unroll
+        for (int d = 0; d < nd; ++d) den[d] = up[c * nd + d].den;
+        recip_all<nd>(den, inv);
+#pragma unroll
+        for (int d = 0; d < nd; ++d)
+            Psi[(c * nd + d) * nc + cc] = mf[c * nd + d] * (up[c * nd + d].q + up[c * nd + d].num * inv[d]);
     }
 }
 
@@ -195,7 +223,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
             o[d] = 1;
             double u1 = load_normal(G, ud, d, P, o[0], o[1], o[2]);
             divu = divu + (u1 - u0) * G.idx[d];
-        } else if (G.g[d] != 0.0) {
+        } else if ((G.gmask >> d) & 1) {
             RE = RE + G.g[d] * (fm0 + fm1);
         }
     }
@@ -215,7 +243,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         double rl = load_cell(G, X, P, o[0], o[1], o[2]);
         double rho_f = 0.5 * (rl + rho);
         double Rc = -(pc - pl) * G.idx[c];
-        if (G.g[c] != 0.0) Rc = Rc + rho_f * G.g[c];
+        if ((G.gmask >> c) & 1) Rc = Rc + rho_f * G.g[c];
 #pragma unroll
         for (int d = 0; d < nd; ++d) {
             const double* ps = Psi + (c * nd + d) * nc;

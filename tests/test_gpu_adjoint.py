@@ -66,7 +66,8 @@ def _small(n=8):
 @pytest.mark.parametrize("n,m", [(8, 30), (16, 30), (16, 4)])
 def test_step_adjoint_parity(jf, n, m):
     """The transposed solve (with restarts when m = 4) gives the oracle's
-    gradients of one converged step."""
+    gradients of one converged step (GMRES to 1e-10: measured 2e-11 to
+    2e-10, asserted 1e-8)."""
     wl, P, dt = _small(n)
     o = jf.default_options(theta=wl.theta, precond=wl.precond, eta=1e-10, reorth=1, gmres_m=m, gmres_max_it=600)
     S = jf.Solver.from_workload(wl, o)
@@ -79,8 +80,10 @@ def test_step_adjoint_parity(jf, n, m):
     assert code == 0, sta
     r = A.step_adjoint(P, wl.X0, X1.cpu(), dt, g, J.Options(precond=wl.precond, eta=1e-10, reorth=1),
                        exact=True)
-    assert _rel(gXn, r.g_Xn) < 1e-7, _rel(gXn, r.g_Xn)
-    assert gK0 == pytest.approx(r.g_K0, rel=1e-7)
+    print("step adjoint n=%d m=%d: g_Xn %.3e g_K0 %.3e its %d" % (n, m, _rel(gXn, r.g_Xn), abs(gK0 / r.g_K0 - 1),
+                                                                 sta["gmres_iterations_total"]))
+    assert _rel(gXn, r.g_Xn) < 1e-8, _rel(gXn, r.g_Xn)
+    assert gK0 == pytest.approx(r.g_K0, rel=1e-8)
 
 
 def _kinetic_energy(P, X):
@@ -123,7 +126,8 @@ def test_autograd_gradient_through_four_steps(jf):
     """Loss = final kinetic energy after four implicit steps of the 8x8
     adjoint problem; gradients with respect to the initial temperature
     perturbation field and to K0 from JFNKStep.backward agree with central
-    differences (1e-5) and with the oracle's dense reference (1e-6)."""
+    differences (1e-5) and with the oracle's dense reference (1e-8; measured
+    about 1e-12)."""
     wl, P, dt = _small(8)
     o = jf.default_options(theta=wl.theta, precond=wl.precond, eta=1e-12, reorth=1)
     X0 = _dev(wl.X0)
@@ -174,8 +178,10 @@ def test_autograd_gradient_through_four_steps(jf):
     dTc = dT.detach().cpu().clone().requires_grad_(True)
     Xi = _initial_state(P, X0.cpu(), dTc)
     (Xi @ g).backward()
-    assert _rel(g_dT, dTc.grad) < 1e-6, _rel(g_dT, dTc.grad)
-    assert g_K0 == pytest.approx(gk, rel=1e-6)
+    print("adjoint vs dense: dT %.3e K0 %.3e; vs FD: dT %.3e K0 %.3e" % (
+        _rel(g_dT, dTc.grad), abs(g_K0 / gk - 1), abs(ad / fd - 1), abs(g_K0 / fdk - 1)))
+    assert _rel(g_dT, dTc.grad) < 1e-8, _rel(g_dT, dTc.grad)
+    assert g_K0 == pytest.approx(gk, rel=1e-8)
 
 
 def test_vjp_rejects_mixed_precision_handles(jf):

@@ -90,6 +90,29 @@ def test_residual_parity(jf, cid, n, form):
         assert float((a - b).abs().max()) <= 1e-9 * float(b.abs().max()) + 1e-300, k
 
 
+@pytest.mark.parametrize("cid,n", [(1, (32, 32)), (3, (16, 16, 16))])
+@pytest.mark.parametrize("uscale", [1e-40, 1e40])
+def test_momentum_flux_parity_at_extreme_velocity_scales(jf, cid, n, uscale):
+    """Uniform rho and e with velocity noise of size uscale, X^n = X and a
+    time step so long that F = -R(X): the momentum rows are then the
+    divergence of the momentum fluxes alone, and the velocity differences
+    lie outside the exponent range of the one-division reciprocals, so the
+    per-slope division path is compared."""
+    wl = W.config(cid, n=n)
+    P = D.Problem.from_workload(wl)
+    nc = P.ncell
+    X = torch.as_tensor(W.random_vector(wl, 11)) * uscale
+    X[:nc] = 1.0
+    X[nc:2 * nc] = 2.0
+    dt = 1e60
+    S = _solver(jf, wl)
+    F = _cpu(S.residual(_dev(X), _dev(X), dt))
+    Fo = D.residual(P, X, X, dt)
+    for k in range(P.nfield):
+        a, b = F[k * nc:(k + 1) * nc], Fo[k * nc:(k + 1) * nc]
+        assert float((a - b).norm() / b.norm()) < 1e-10, k
+
+
 @pytest.mark.parametrize("cid,n,form", CASES)
 def test_scaling_parity(jf, cid, n, form):
     wl, P, X, Xn, dt = _case(cid, n, form)
@@ -137,6 +160,23 @@ def test_precond_parity(jf, cid, n, form, pc):
             idx = [slice(None)] * 3
             idx[2 - c] = 0
             assert float(f[tuple(idx)].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("cid,n,form,pc", PC_CASES)
+def test_precond_parity_fp32(jf, cid, n, form, pc):
+    """The FP32 preconditioner (FP32 multigrid with cell-field coefficients
+    on the finest level, folded transform coefficients) against the FP64
+    oracle.  Its error is FP32 rounding (6e-8) amplified by the conditioning
+    of the semi-implicit system, largest at the highest CFL numbers here
+    (measured 1e-7 to 3e-5); 1e-4 bounds it with margin."""
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    v = torch.as_tensor(W.random_vector(wl, 5))
+    o = jf.default_options(theta=wl.theta, precond=pc, mg_cycles=2, precision=jf.MIXED)
+    S = jf.Solver.from_workload(wl, o)
+    w = S.precond_apply(_dev(X), dt, _dev(v).float())
+    oo = J.Options(precond=pc, mg_cycles=2)
+    wo = PC.apply(PC.setup(P, X, dt, oo), v, J.scaling(P, X, oo))
+    assert _relnorm(w, wo) < 1e-4
 
 
 @pytest.mark.parametrize("cid,n,pc,m,its", [(1, (32, 32), 1, 8, 12), (2, (32, 32), 2, 10, 10),
