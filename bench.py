@@ -313,8 +313,10 @@ def main():
     ap.add_argument("--mg-cycles", type=int, default=None, help="multigrid V-cycles per preconditioner apply")
     ap.add_argument("--mg-nu1", type=int, default=None, help="pre-smoothing sweeps")
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
+    ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
+                    help="1: preconditioner coefficients from X^n for the whole step")
     args = ap.parse_args()
-    for k in ("mg_cycles", "mg_nu1", "mg_nu2"):
+    for k in ("mg_cycles", "mg_nu1", "mg_nu2", "pc_freeze"):
         if getattr(args, k) is not None:
             OPT_OVERRIDES[k] = getattr(args, k)
     if args.only:
@@ -345,7 +347,7 @@ def main():
     S, X0, dt, ms_mixed, st_mixed = run_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream, True)
     so = S.options
     solver_cfg = {"newton_tol": NEWTON_TOL, "eta": ETA, "gmres_m": so.gmres_m, "precond": so.precond,
-                  "mg_cycles": so.mg_cycles, "mg_nu1": so.mg_nu1, "mg_nu2": so.mg_nu2}
+                  "mg_cycles": so.mg_cycles, "mg_nu1": so.mg_nu1, "mg_nu2": so.mg_nu2, "pc_freeze": so.pc_freeze}
     barrier(ws)
     clk = clocks.stop()
     ms_mixed = max_over_ranks(ws, ms_mixed)

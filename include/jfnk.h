@@ -82,14 +82,19 @@ typedef struct { double K0; double exponent; } jfnk_conductivity;
  * (Eq. jacobian_system_norm), eta = 1e-4 (Eq. forcing_term).  gmres_m is the
  * restart length, gmres_max_it the total iteration cap per linear solve,
  * newton_min = 2 forces the second iteration of Sect. 4.1.  mg_cycles V-cycles
- * with mg_nu1 / mg_nu2 red-black Gauss-Seidel sweeps solve the semi-implicit
- * system.  reorth = 1 adds a second classical Gram-Schmidt pass.
+ * (default 1) with mg_nu1 / mg_nu2 (default 2 / 2) red-black Gauss-Seidel
+ * sweeps solve the semi-implicit system.  reorth = 1 adds a second classical Gram-Schmidt pass.
  * fixed_iterations = 1 runs exactly gmres_max_it iterations per linear solve
- * and newton_max Newton iterations (reproducible iteration counts). */
+ * and newton_max Newton iterations (reproducible iteration counts).
+ * pc_freeze = 1 takes the semi-implicit coefficients and transforms of the
+ * preconditioner from X^n, the time level at which Sects. 3.3-3.4 write them,
+ * for every Newton iteration of a step (only the scaling L, R follows the
+ * iterate); 0 (default) rebuilds them at every Newton iterate. */
 typedef struct {
     double theta, lambda, alpha1, alpha2, eta, newton_tol;
     int pert, gmres_m, gmres_max_it, newton_min, newton_max;
     int precond, mg_cycles, mg_nu1, mg_nu2, precision, reorth, fixed_iterations;
+    int pc_freeze;
 } jfnk_options;
 
 #define JFNK_MAX_NEWTON 64
@@ -211,7 +216,7 @@ jfnk_status jfnk_set_profiling(jfnk_handle* h, int on);
  * memory.  The paper has no counterpart: this is an interface variant.
  * Same arguments, layout and result as jfnk_residual, but the scratch it needs
  * (b^n, p, T and the flux fields) lives in a fixed array inside the library
- * (JFNK_NOALLOC_MAX_CELLS * 22 doubles, 11.5 MB, held on every GPU that loads
+ * (JFNK_NOALLOC_MAX_CELLS * 23 doubles, 12.1 MB, held on every GPU that loads
  * the library until the process exits) instead of the bound workspace, so
  * the handle needs no jfnk_bind and the call allocates nothing.  Grids above
  * JFNK_NOALLOC_MAX_CELLS cells return JFNK_EINVAL with a message.  The first

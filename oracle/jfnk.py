@@ -50,12 +50,13 @@ class Options:
     newton_min: int = 2
     newton_max: int = 20
     precond: int = 1               # 0 none, 1 sound, 2 sound + diffusion
-    mg_cycles: int = 2
+    mg_cycles: int = 1              # one V(mg_nu1, mg_nu2) cycle per preconditioner apply
     mg_nu1: int = 2
     mg_nu2: int = 2
     reorth: int = 0                # 1: always a second Gram-Schmidt pass
     fixed_iterations: bool = False # run exactly gmres_max_it / newton_max iterations
     exact_inner: bool = False      # solve the SI system with a sparse direct solver
+    pc_freeze: bool = False        # SI coefficients from X^n (Sects. 3.3-3.4 write them at level n)
 
 
 # ----------------------------------------------------------------------------
@@ -229,14 +230,18 @@ def newton_step(P: D.Problem, Xn, dt: float, opts: Options, on_iterate=None):
     bn = D.bn_constant(P, Xn, dt)
     X = Xn.clone()
     st = StepStats()
+    si = None
     for k in range(opts.newton_max):
         sc = scaling(P, X, opts)
         G0 = D.G_operator(P, X, dt)
         Fhat = (G0 - bn) / sc.L
         st.fhat_norm.append(float(torch.linalg.vector_norm(Fhat)))
         if opts.precond:
-            si = PC.setup(P, X, dt, opts)
-            Minv = lambda v: PC.apply(si, v, sc)           # noqa: E731
+            # pc_freeze: the setup at X^(0) = X^n serves every iterate of the
+            # step; the scaling sc still follows the iterate
+            if si is None or not opts.pc_freeze:
+                si = PC.setup(P, X, dt, opts)
+            Minv = lambda v, si=si: PC.apply(si, v, sc)    # noqa: E731
         else:
             Minv = lambda v: v                             # noqa: E731
 

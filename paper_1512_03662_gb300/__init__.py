@@ -54,7 +54,7 @@ class jfnk_options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("theta", "lambda_", "alpha1", "alpha2", "eta", "newton_tol")] + \
                [(n, ctypes.c_int) for n in ("pert", "gmres_m", "gmres_max_it", "newton_min", "newton_max",
                                              "precond", "mg_cycles", "mg_nu1", "mg_nu2", "precision", "reorth",
-                                             "fixed_iterations")]
+                                             "fixed_iterations", "pc_freeze")]
 
 
 class jfnk_stats(ctypes.Structure):
@@ -135,10 +135,16 @@ class JFNKError(RuntimeError):
 
 
 def default_options(**kw) -> jfnk_options:
+    """jfnk_default_options with the given fields replaced (lam for lambda);
+    an unknown field name raises instead of being ignored."""
     o = jfnk_options()
     lib().jfnk_default_options(ctypes.byref(o))
+    names = {f[0] for f in jfnk_options._fields_}
     for k, v in kw.items():
-        setattr(o, "lambda_" if k == "lam" else k, v)
+        k = "lambda_" if k == "lam" else k
+        if k not in names:
+            raise TypeError(f"unknown jfnk option {k!r}")
+        setattr(o, k, v)
     return o
 
 

@@ -16,6 +16,7 @@ struct Grid {
     int n[3];
     long long ncell;
     double dx[3], idx[3], idx2[3], tidx[3];   // tidx = 2 / dx
+    double hidx[3];                           // 0.5 / dx
     int bc[3];                       // 0 periodic, 1 wall
     double gamma, gm1;
     double g[3];

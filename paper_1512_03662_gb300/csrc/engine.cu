@@ -34,7 +34,7 @@ struct jfnk_handle {
     int profiling;
     cudaEvent_t ev[16];
     // workspace carve-up
-    double *bn, *G0, *L, *R, *Linv, *Rinv, *Xp, *dxh, *p, *T, *Fm, *FE, *Psi, *partials, *scal;
+    double *bn, *G0, *L, *R, *Linv, *Rinv, *Xp, *dxh, *p, *T, *chi, *Fm, *FE, *Psi, *partials, *scal;
     double *H, *cs, *sn, *g, *y, *vscale, *hc2;
     void *V, *Z, *rp, *re, *ru, *C;
     // adjoint (FP64): VJP scratch, its output, transposed-preconditioner
@@ -90,6 +90,7 @@ size_t plan(jfnk_handle* h, char* base) {
     h->dxh = (double*)take(nv * 8);
     h->p = (double*)take(nc * 8);
     h->T = (double*)take(nc * 8);
+    h->chi = (double*)take(nc * 8);
     h->Fm = (double*)take(nd * nc * 8);
     h->FE = (double*)take(nd * nc * 8);
     h->Psi = (double*)take((long long)nd * nd * nc * 8);
@@ -177,8 +178,8 @@ unsigned cblocks(jfnk_handle* h) { return cell_blocks(h->G); }
 template <int MODE, typename TO>
 void eval(jfnk_handle* h, const double* Xs, double dt, double* outd, TO* outb) {
     cudaStream_t s = h->stream;
-    launch_eos(h->G, Xs, h->p, h->T, s);
-    launch_fluxes(h->G, Xs, h->p, h->T, h->Fm, h->FE, h->Psi, s);
+    launch_eos(h->G, Xs, h->p, h->T, h->chi, s);
+    launch_fluxes(h->G, Xs, h->p, h->T, h->chi, h->Fm, h->FE, h->Psi, s);
     launch_assemble<MODE, TO>(h->G, Xs, h->p, h->Fm, h->FE, h->Psi, h->bn, h->G0, h->Linv, h->scal, kSlotDelta, dt,
                               outd, outb, s);
 }
@@ -266,9 +267,9 @@ void jv(jfnk_handle* h, const double* X, double dt, const TZ* z, int znorm_ready
     if (prof) cudaEventRecord(h->ev[0], s);
     launch_perturb<TZ>(h->G, X, z, h->R, h->scal, kSlotDelta, h->Xp, s);
     if (prof) cudaEventRecord(h->ev[1], s);
-    launch_eos(h->G, h->Xp, h->p, h->T, s);
+    launch_eos(h->G, h->Xp, h->p, h->T, h->chi, s);
     if (prof) cudaEventRecord(h->ev[2], s);
-    launch_face_fluxes(h->G, h->Xp, h->p, h->T, h->Fm, h->FE, s);
+    launch_face_fluxes(h->G, h->Xp, h->p, h->T, h->chi, h->Fm, h->FE, s);
     if (prof) cudaEventRecord(h->ev[3], s);
     launch_mom_fluxes(h->G, h->Xp, h->Fm, h->Psi, s);
     if (prof) cudaEventRecord(h->ev[4], s);
@@ -400,17 +401,24 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
     }
 }
 
-// scaling, G0, RHS in V[0], SI coefficients at iterate X (b^n must be set)
+// scaling, G0, RHS in V[0] and the preconditioner at iterate X (b^n must be
+// set); full_setup = false keeps the SI coefficients of the previous setup
+// and renews only the scaling fields
 template <typename T>
-void linearize(jfnk_handle* h, const double* X, double dt) {
+void linearize(jfnk_handle* h, const double* X, double dt, bool full_setup) {
     scaling(h, X);
     eval<kModeNewton, T>(h, X, dt, h->G0, Vcol<T>(h, 0));
-    si_setup(h, X, dt);
+    if (full_setup) {
+        si_setup(h, X, dt);
+    } else if (h->nf > 0) {
+        if (h->mixed) launch_pc_rescale<float>(h->G, h->L, h->Rinv, (float*)h->C, h->stream);
+        else launch_pc_rescale<double>(h->G, h->L, h->Rinv, (double*)h->C, h->stream);
+    }
 }
 
 template <typename T>
-jfnk_status newton_solve(jfnk_handle* h, const double* X, double dt, double eta, SolveOut& so) {
-    linearize<T>(h, X, dt);
+jfnk_status newton_solve(jfnk_handle* h, const double* X, double dt, double eta, SolveOut& so, bool full_setup) {
+    linearize<T>(h, X, dt, full_setup);
     return gmres<T>(h, X, dt, eta, so);
 }
 
@@ -421,8 +429,8 @@ jfnk_status newton_solve(jfnk_handle* h, const double* X, double dt, double eta,
 // out = (a dU/dX + b dR/dX)^T w at Xs
 void vjp_apply(jfnk_handle* h, const double* Xs, const double* w, double a, double b, double* out) {
     cudaStream_t s = h->stream;
-    launch_eos(h->G, Xs, h->p, h->T, s);
-    launch_face_fluxes(h->G, Xs, h->p, h->T, h->Fm, h->FE, s);
+    launch_eos(h->G, Xs, h->p, h->T, h->chi, s);
+    launch_face_fluxes(h->G, Xs, h->p, h->T, h->chi, h->Fm, h->FE, s);
     launch_vjp(h->G, Xs, h->p, h->T, h->Fm, w, a, b, h->adj, out, s);
 }
 
@@ -531,6 +539,7 @@ jfnk_status validate_options(jfnk_handle* h, const jfnk_options* o) {
     if (o->precond < 0 || o->precond > 2) return fail(h, JFNK_EINVAL, "unknown preconditioner");
     if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return fail(h, JFNK_EINVAL, "unknown precision");
     if (o->mg_cycles < 1 || o->mg_nu1 < 0 || o->mg_nu2 < 0) return fail(h, JFNK_EINVAL, "bad multigrid cycle counts");
+    if (o->pc_freeze != 0 && o->pc_freeze != 1) return fail(h, JFNK_EINVAL, "pc_freeze must be 0 or 1");
     if (!(o->lambda > 0.0)) return fail(h, JFNK_EINVAL, "lambda must be positive");
     if (o->pert != JFNK_PERT_OLD && o->pert != JFNK_PERT_NEW) return fail(h, JFNK_EINVAL, "unknown perturbation rule");
     return JFNK_OK;
@@ -560,12 +569,13 @@ void jfnk_default_options(jfnk_options* o) {
     o->newton_min = 2;
     o->newton_max = 20;
     o->precond = JFNK_PRECOND_SOUND;
-    o->mg_cycles = 2;
+    o->mg_cycles = 1;
     o->mg_nu1 = 2;
     o->mg_nu2 = 2;
     o->precision = JFNK_FP64;
     o->reorth = 0;
     o->fixed_iterations = 0;
+    o->pc_freeze = 0;
 }
 
 jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_gravity* gravity,
@@ -601,6 +611,7 @@ jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_g
         G.idx[d] = 1.0 / G.dx[d];
         G.idx2[d] = G.idx[d] * G.idx[d];
         G.tidx[d] = 2.0 * G.idx[d];
+        G.hidx[d] = 0.5 * G.idx[d];
     }
     G.ncell = (long long)G.n[0] * G.n[1] * G.n[2];
     if (!(eos->gamma > 1.0)) { *out = h; return fail(h, JFNK_EINVAL, "gamma must exceed 1"); }
@@ -723,7 +734,8 @@ jfnk_status jfnk_linear_solve(jfnk_handle* h, const double* X, const double* Xn,
     if (!X || !Xn || !dxhat || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_linear_solve");
     eval<kModeBn, double>(h, Xn, dt, h->bn, (double*)nullptr);
     SolveOut so;
-    st = h->mixed ? newton_solve<float>(h, X, dt, h->opt.eta, so) : newton_solve<double>(h, X, dt, h->opt.eta, so);
+    st = h->mixed ? newton_solve<float>(h, X, dt, h->opt.eta, so, true)
+                  : newton_solve<double>(h, X, dt, h->opt.eta, so, true);
     if (st < 0) return st;
     CUDA_TRY(h, cudaMemcpyAsync(dxhat, h->dxh, h->nvec * 8, cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -757,7 +769,9 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
     bool gmres_fail = false;
     for (int k = 0; k < h->opt.newton_max; ++k) {
         SolveOut so;
-        st = h->mixed ? newton_solve<float>(h, X, dt, eta, so) : newton_solve<double>(h, X, dt, eta, so);
+        // X^(0) = X^n: with pc_freeze the first setup is the one at X^n
+        const bool full = k == 0 || !h->opt.pc_freeze;
+        st = h->mixed ? newton_solve<float>(h, X, dt, eta, so, full) : newton_solve<double>(h, X, dt, eta, so, full);
         if (st < 0) return st;
         launch_newton_update(X, h->R, h->dxh, h->nvec, h->partials, h->stream);
         launch_finalize(h->partials, kRedBlocks, h->scal, kSlotDxInf, 2, h->stream);
@@ -818,7 +832,7 @@ jfnk_status jfnk_vjp(jfnk_handle* h, const double* Xn, const double* Xnp1, doubl
         const double wts[2] = {h->opt.theta, 1.0 - h->opt.theta};
         const double* states[2] = {Xnp1, Xn};
         for (int q = 0; q < 2; ++q) {
-            launch_eos(h->G, states[q], h->p, h->T, s);
+            launch_eos(h->G, states[q], h->p, h->T, h->chi, s);
             launch_dRdK0_dot(h->G, h->T, h->lam, h->partials, s);
             launch_finalize(h->partials, (int)cblocks(h), h->scal, kSlotTmp, 1, s);
             if ((st = sync_read(h)) != JFNK_OK) return st;

@@ -25,15 +25,16 @@ enum {
 };
 
 // residual.cu
-void launch_eos(const Grid& G, const double* X, double* p, double* T, cudaStream_t s);
+// p, T and, when the grid has conduction, chi = K0 T^exp per cell
+void launch_eos(const Grid& G, const double* X, double* p, double* T, double* chi, cudaStream_t s);
 template <typename TZ>
 void launch_perturb(const Grid& G, const double* X, const TZ* z, const double* R, const double* scal, int slot,
                     double* Xp, cudaStream_t s);
-void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
-                        cudaStream_t s);
+void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, const double* chi,
+                        double* Fm, double* FE, cudaStream_t s);
 void launch_mom_fluxes(const Grid& G, const double* X, const double* Fm, double* Psi, cudaStream_t s);
-void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
-                   double* Psi, cudaStream_t s);
+void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, const double* chi, double* Fm,
+                   double* FE, double* Psi, cudaStream_t s);
 template <int MODE, typename TO>
 void launch_assemble(const Grid& G, const double* X, const double* p, const double* Fm, const double* FE,
                      const double* Psi, const double* bn, const double* G0, const double* Linv, const double* scal,
@@ -111,6 +112,9 @@ void launch_pc_setup(const Grid& G, const double* X, const double* L, const doub
                      MGLevel& L0, cudaStream_t s);
 template <typename T>
 void launch_coarsen(const Grid& G, int nf, const MGLevel& F, MGLevel& C, cudaStream_t s);
+// renew only the scaling fields (L and R^-1) of the coefficient array C
+template <typename T>
+void launch_pc_rescale(const Grid& G, const double* L, const double* Rinv, T* C, cudaStream_t s);
 // zero_x = 1: also zero the level-0 multigrid unknowns (needed when the
 // V-cycle does not start with a zero-start half sweep)
 template <typename T>

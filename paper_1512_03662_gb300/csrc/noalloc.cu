@@ -12,7 +12,7 @@
 // a created handle (no jfnk_bind).
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (JFNK_NOALLOC_MAX_CELLS * 22 doubles, 11.5 MB) until the
+// library holds it (JFNK_NOALLOC_MAX_CELLS * 23 doubles, 12.1 MB) until the
 // process exits.  Host code reaches it only through the address returned by
 // cudaGetSymbolAddress, fetched once per device on the first call made with
 // that device current.  Every call shares the one array, so calls that
@@ -30,7 +30,7 @@ using namespace jfnk;
 
 namespace {
 
-constexpr long long kNoallocFields = 22;   // 5 b^n + p + T + 3 Fm + 3 FE + 9 Psi (3D; 2D uses 14)
+constexpr long long kNoallocFields = 23;   // 5 b^n + p + T + chi + 3 Fm + 3 FE + 9 Psi (3D; 2D uses 15)
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_noalloc_scratch[kNoallocFields * JFNK_NOALLOC_MAX_CELLS];
@@ -86,16 +86,17 @@ extern "C" jfnk_status jfnk_residual_noalloc(jfnk_handle* h, const double* X, co
     double* bn = base;
     double* p = bn + (2 + nd) * nc;
     double* T = p + nc;
-    double* Fm = T + nc;
+    double* chi = T + nc;
+    double* Fm = chi + nc;
     double* FE = Fm + nd * nc;
     double* Psi = FE + nd * nc;
     cudaStream_t s = jfnk_handle_stream(h);
-    launch_eos(G, Xn, p, T, s);
-    launch_fluxes(G, Xn, p, T, Fm, FE, Psi, s);
+    launch_eos(G, Xn, p, T, chi, s);
+    launch_fluxes(G, Xn, p, T, chi, Fm, FE, Psi, s);
     launch_assemble<kModeBn, double>(G, Xn, p, Fm, FE, Psi, nullptr, nullptr, nullptr, nullptr, 0, dt, bn,
                                      (double*)nullptr, s);
-    launch_eos(G, X, p, T, s);
-    launch_fluxes(G, X, p, T, Fm, FE, Psi, s);
+    launch_eos(G, X, p, T, chi, s);
+    launch_fluxes(G, X, p, T, chi, Fm, FE, Psi, s);
     launch_assemble<kModeRes, double>(G, X, p, Fm, FE, Psi, bn, nullptr, nullptr, nullptr, 0, dt, F,
                                       (double*)nullptr, s);
     e = cudaGetLastError();

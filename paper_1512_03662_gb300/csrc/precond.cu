@@ -221,6 +221,33 @@ template void launch_pc_setup<double>(const Grid&, const double*, const double*,
 template void launch_pc_setup<float>(const Grid&, const double*, const double*, const double*, double, int, float*,
                                      MGLevel&, cudaStream_t);
 
+// The scaling fields of C alone, as k_pc_setup writes them (the frozen-
+// coefficient option renews only these at later Newton iterates).
+template <int ND, typename T>
+__global__ void k_pc_rescale(Grid G, const double* __restrict__ L, const double* __restrict__ Rinv,
+                             T* __restrict__ C) {
+    Idx3 P;
+    long long cc;
+    if (!cell_pos(G.n, P, cc)) return;
+    const long long nc = G.ncell;
+    C[PcLr * nc + cc] = (T)L[cc];
+    C[PcLE * nc + cc] = (T)L[nc + cc];
+    C[PcRinvR * nc + cc] = (T)Rinv[cc];
+    C[PcRinvE * nc + cc] = (T)Rinv[nc + cc];
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+        C[(PcLu + c) * nc + cc] = (T)L[(2 + c) * nc + cc];
+        C[(PcRinvU + c) * nc + cc] = (T)Rinv[(2 + c) * nc + cc];
+    }
+}
+
+template <typename T>
+void launch_pc_rescale(const Grid& G, const double* L, const double* Rinv, T* C, cudaStream_t s) {
+    CELL_LAUNCH_T(k_pc_rescale, T, G, L, Rinv, C);
+}
+template void launch_pc_rescale<double>(const Grid&, const double*, const double*, double*, cudaStream_t);
+template void launch_pc_rescale<float>(const Grid&, const double*, const double*, float*, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 // coarse coefficients
 // ---------------------------------------------------------------------------

@@ -35,8 +35,15 @@ __global__ void k_perturb(Grid G, const double* __restrict__ X, const TZ* __rest
     Xp[k] = X[k] + delta * (R[k] * (double)z[k]);
 }
 
+__device__ __forceinline__ double conductivity(const Grid& G, double T) {
+    return G.chi3 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+}
+
+// p, T and (with conduction) chi = K0 T^exp per cell, each formed once for
+// all the faces that use it
 template <int ND>
-__global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__ p, double* __restrict__ T) {
+__global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__ p, double* __restrict__ T,
+                      double* __restrict__ chi) {
     Idx3 P;
     long long c;
     if (!cell_pos(G.n, P, c)) return;
@@ -57,16 +64,15 @@ __global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__
         e = e - ke;
     }
     p[c] = G.gm1 * rho * e;
-    T[c] = G.gm1 * e;
-}
-
-__device__ __forceinline__ double conductivity(const Grid& G, double T) {
-    return G.chi3 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+    const double Tc = G.gm1 * e;
+    T[c] = Tc;
+    if (G.has_cond) chi[c] = conductivity(G, Tc);
 }
 
 template <int ND>
 __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ p,
-                              const double* __restrict__ T, double* __restrict__ Fmh, double* __restrict__ FE) {
+                              const double* __restrict__ T, const double* __restrict__ chi, double* __restrict__ Fmh,
+                              double* __restrict__ FE) {
     Idx3 P;
     long long c;
     if (!cell_pos(G.n, P, c)) return;
@@ -107,10 +113,11 @@ __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double
             fe = fe + 0.5 * (pl + __ldg(p + c)) * u[d];
         }
         if (G.has_cond) {
-            double Tl = load_cell(G, T, P, o[0], o[1], o[2]);
-            double Tc = __ldg(T + c);
-            double q = 0.5 * (conductivity(G, Tl) + conductivity(G, Tc)) * (Tc - Tl) * G.idx[d];
-            fe = fe - q;
+            // q = chi_f (T_c - T_l) / dx with chi_f the mean of the two cells
+            const double Tl = load_cell(G, T, P, o[0], o[1], o[2]);
+            const double chil = load_cell(G, chi, P, o[0], o[1], o[2]);
+            const double sq = (chil + __ldg(chi + c)) * G.hidx[d];
+            fe = fma(-sq, __ldg(T + c) - Tl, fe);
         }
         Fmh[d * nc + c] = 0.5 * fm;           // half mass flux: every consumer averages two of them
         FE[d * nc + c] = fe;
@@ -390,8 +397,8 @@ static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / 
         else KERNEL<2><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);                       \
     } while (0)
 
-void launch_eos(const Grid& G, const double* X, double* p, double* T, cudaStream_t s) {
-    CELL_LAUNCH(k_eos, G, X, p, T);
+void launch_eos(const Grid& G, const double* X, double* p, double* T, double* chi, cudaStream_t s) {
+    CELL_LAUNCH(k_eos, G, X, p, T, chi);
 }
 
 template <typename TZ>
@@ -406,18 +413,18 @@ template void launch_perturb<double>(const Grid&, const double*, const double*, 
 template void launch_perturb<float>(const Grid&, const double*, const float*, const double*, const double*, int,
                                     double*, cudaStream_t);
 
-void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
-                        cudaStream_t s) {
-    CELL_LAUNCH(k_face_fluxes, G, X, p, T, Fm, FE);
+void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, const double* chi,
+                        double* Fm, double* FE, cudaStream_t s) {
+    CELL_LAUNCH(k_face_fluxes, G, X, p, T, chi, Fm, FE);
 }
 
 void launch_mom_fluxes(const Grid& G, const double* X, const double* Fm, double* Psi, cudaStream_t s) {
     CELL_LAUNCH(k_mom_fluxes, G, X, Fm, Psi);
 }
 
-void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, double* Fm, double* FE,
-                   double* Psi, cudaStream_t s) {
-    launch_face_fluxes(G, X, p, T, Fm, FE, s);
+void launch_fluxes(const Grid& G, const double* X, const double* p, const double* T, const double* chi, double* Fm,
+                   double* FE, double* Psi, cudaStream_t s) {
+    launch_face_fluxes(G, X, p, T, chi, Fm, FE, s);
     launch_mom_fluxes(G, X, Fm, Psi, s);
 }
 

@@ -124,6 +124,34 @@ def test_scaling_parity(jf, cid, n, form):
     assert xn == pytest.approx(sc.xhat_norm, rel=1e-13)
 
 
+@pytest.mark.parametrize("cid,n,form", [CASES[0], CASES[1], CASES[3], CASES[5], CASES[6]])
+@pytest.mark.parametrize("alpha1,alpha2", [(1.0, 1.0), (1e-5, 0.5)])
+def test_scaling_parity_alpha_variants(jf, cid, n, form, alpha1, alpha2):
+    """The velocity scalings of Eq. jacobian_system_norm with the other
+    alpha choices of Sect. 4.2 (alpha1 = 1 scales by the sound speed)."""
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    S = _solver(jf, wl, alpha1=alpha1, alpha2=alpha2)
+    L, R, xn = S.scaling(_dev(X))
+    sc = J.scaling(P, X, J.Options(alpha1=alpha1, alpha2=alpha2))
+    assert _relnorm(L, sc.L) < 1e-14
+    assert _relnorm(R, sc.R) < 1e-14
+    assert xn == pytest.approx(sc.xhat_norm, rel=1e-13)
+
+
+@pytest.mark.parametrize("cid,n,form", CASES)
+def test_jv_parity_pert_new(jf, cid, n, form):
+    """Jv with the perturbation of Eq. pert_new (sign and size from x^ . w)."""
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    v = torch.as_tensor(W.random_vector(wl, 3))
+    S = _solver(jf, wl, lam=1e-4, pert=1)
+    Jv, delta = S.jv(_dev(X), dt, _dev(v))
+    oo = J.Options(lam=1e-4, pert=J.PERT_NEW)
+    sc = J.scaling(P, X, oo)
+    Jo, do = J.jv(P, X, D.G_operator(P, X, dt), sc, v, dt, oo)
+    assert delta == pytest.approx(do, rel=1e-12)
+    assert _relnorm(Jv, Jo) < 1e-10, _relnorm(Jv, Jo)
+
+
 @pytest.mark.parametrize("cid,n,form", CASES)
 def test_jv_parity(jf, cid, n, form):
     wl, P, X, Xn, dt = _case(cid, n, form)
@@ -201,15 +229,19 @@ def test_linear_solve_parity_fixed_iterations(jf, cid, n, pc, m, its):
     assert _relnorm(dx, dxo) < 1e-9, _relnorm(dx, dxo)
 
 
-def test_step_parity_fixed_iterations(jf):
+@pytest.mark.parametrize("variant", [{}, {"pert": 1}, {"alpha1": 1.0}, {"pc_freeze": 1}])
+def test_step_parity_fixed_iterations(jf, variant):
+    """Three Newton iterations of ten GMRES iterations each, with the default
+    settings, the parameter variants of Sects. 4.2 and 5.1.1, and the
+    preconditioner frozen at X^n."""
     wl, P, X, Xn, dt = _case(1, (32, 32), 0, cfl=10.0)
     o = jf.default_options(theta=wl.theta, precond=1, gmres_m=10, gmres_max_it=10, newton_max=3,
-                           fixed_iterations=1, lam=1e-4)
+                           fixed_iterations=1, lam=1e-4, **variant)
     S = jf.Solver.from_workload(wl, o)
     Xg = _dev(Xn)
     st = S.step(Xg, dt)
     assert st["newton_iterations"] == 3
-    oo = J.Options(precond=1, gmres_m=10, gmres_max_it=10, newton_max=3, fixed_iterations=True, lam=1e-4)
+    oo = J.Options(precond=1, gmres_m=10, gmres_max_it=10, newton_max=3, fixed_iterations=True, lam=1e-4, **variant)
     Xo, sto = J.newton_step(P, Xn, dt, oo)
     sc = J.scaling(P, Xn, oo)
     assert _relnorm(Xg - _dev(Xn), Xo - Xn, sc.R) < 1e-8

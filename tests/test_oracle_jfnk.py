@@ -295,6 +295,30 @@ def test_newton_step_solves_the_residual_equation():
         assert abs(lhs - rhs_) < 1e-13 * float(U0[k].abs().sum()) + 1e-15
 
 
+def test_frozen_preconditioner_reaches_the_same_step():
+    """With the SI coefficients frozen at X^n (pc_freeze) the first Newton
+    iteration is unchanged (X^(0) = X^n) and the step converges to the same
+    X^{n+1}: the preconditioner changes the path, not the root of F_U."""
+    wl = W.config(2, n=(32, 32))
+    P = D.Problem.from_workload(wl)
+    X0 = torch.as_tensor(wl.X0)
+    dt = D.cfl_dt(P, X0, 20.0)
+    first = {}
+
+    def grab(tag):
+        def f(k, X, dxh, gs):
+            if k == 0:
+                first[tag] = (dxh.clone(), gs.iterations)
+        return f
+    o = dict(precond=2, newton_tol=1e-11, eta=1e-8)
+    X1, st = J.newton_step(P, X0, dt, J.Options(**o), on_iterate=grab("refresh"))
+    X2, st2 = J.newton_step(P, X0, dt, J.Options(pc_freeze=True, **o), on_iterate=grab("freeze"))
+    assert st.converged and st2.converged
+    assert torch.equal(first["refresh"][0], first["freeze"][0])
+    sc = J.scaling(P, X1, J.Options())
+    assert float(((X1 - X2) / sc.R).abs().max()) < 1e-9
+
+
 def test_unpreconditioned_gmres_stalls_at_large_cfl():
     """Sect. 5.1.1: without preconditioning GMRES does not converge for
     CFL_hydro >~ 10; with the sound-wave PBP it does."""
