@@ -82,7 +82,7 @@ typedef struct { double K0; double exponent; } jfnk_conductivity;
  * (Eq. jacobian_system_norm), eta = 1e-4 (Eq. forcing_term).  gmres_m is the
  * restart length, gmres_max_it the total iteration cap per linear solve,
  * newton_min = 2 forces the second iteration of Sect. 4.1.  mg_cycles V-cycles
- * (default 1) with mg_nu1 / mg_nu2 (default 2 / 2) red-black Gauss-Seidel
+ * (default 2) with mg_nu1 / mg_nu2 (default 2 / 2) red-black Gauss-Seidel
  * sweeps solve the semi-implicit system.  reorth = 1 adds a second classical Gram-Schmidt pass.
  * fixed_iterations = 1 runs exactly gmres_max_it iterations per linear solve
  * and newton_max Newton iterations (reproducible iteration counts).

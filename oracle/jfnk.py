@@ -50,7 +50,7 @@ class Options:
     newton_min: int = 2
     newton_max: int = 20
     precond: int = 1               # 0 none, 1 sound, 2 sound + diffusion
-    mg_cycles: int = 1              # one V(mg_nu1, mg_nu2) cycle per preconditioner apply
+    mg_cycles: int = 2              # V(mg_nu1, mg_nu2) cycles per preconditioner apply
     mg_nu1: int = 2
     mg_nu2: int = 2
     reorth: int = 0                # 1: always a second Gram-Schmidt pass

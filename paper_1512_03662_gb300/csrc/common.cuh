@@ -27,6 +27,7 @@ struct Grid {
     // on them without FP64 compares: bit d of gmask = (g[d] != 0),
     // has_cond = (K0 != 0), chi3 = (chi_exp == 3)
     int gmask, has_cond, chi3;
+    double igm1, igamma;             // 1/(gamma-1) = c_v and 1/gamma, formed on the host
 };
 
 inline void set_grid_flags(Grid& G) {
@@ -35,6 +36,8 @@ inline void set_grid_flags(Grid& G) {
         if (G.g[d] != 0.0) G.gmask |= 1 << d;
     G.has_cond = G.K0 != 0.0;
     G.chi3 = G.chi_exp == 3.0;
+    G.igm1 = 1.0 / G.gm1;
+    G.igamma = 1.0 / G.gamma;
 }
 
 struct Idx3 { int i[3]; };

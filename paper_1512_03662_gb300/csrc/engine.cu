@@ -569,7 +569,7 @@ void jfnk_default_options(jfnk_options* o) {
     o->newton_min = 2;
     o->newton_max = 20;
     o->precond = JFNK_PRECOND_SOUND;
-    o->mg_cycles = 1;
+    o->mg_cycles = 2;
     o->mg_nu1 = 2;
     o->mg_nu2 = 2;
     o->precision = JFNK_FP64;

@@ -94,88 +94,94 @@ __device__ __forceinline__ double e_internal_at(const Grid& G, const double* X, 
     return E - ke;
 }
 
-struct Binv2 { double b00, b01, b10, b11, bpp; };
-
-__device__ __forceinline__ Binv2 si_B(const Grid& G, double rho, double p, double dt, int nf) {
-    const double th = G.theta;
-    Binv2 B;
-    B.bpp = th * th * dt * G.gamma * p;
-    if (nf == 2) {
-        double bpe = th * (G.gamma - 1.0);
-        double bep = th * th * dt * p / rho;
-        double bee = th / rho;
-        double det = B.bpp * bee - bpe * bep;
-        B.b00 = bee / det;
-        B.b01 = -bpe / det;
-        B.b10 = -bep / det;
-        B.b11 = B.bpp / det;
-    } else {
-        B.b00 = B.b01 = B.b10 = B.b11 = 0.0;
-    }
-    return B;
-}
-
-
 // Per-cell coefficient fields of the transforms, in the basis precision T.
 // Field order (index * ncell): see PcField.  All divisions of the
-// preconditioner happen here, once per Newton iteration.
+// preconditioner happen here, once per Newton iteration, and they reduce to
+// reciprocals of rho, e, b_pp and the face densities (one batched
+// inversion) and of det B: every other quotient is a product with those.
+// B is the 2x2 matrix of Laplacian coefficients of the p and e rows (sound
+// scheme: b_pp alone), B^-1 its inverse.
 template <int ND, typename T>
 __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* __restrict__ L,
-                           const double* __restrict__ Rinv, double dt, int nf, T* __restrict__ C,
+                           const double* __restrict__ Rinv, double dt, double idt, int nf, T* __restrict__ C,
                            T* __restrict__ M, T* __restrict__ K) {
     Idx3 P;
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
-    double rho = X[cc];
-    double E = X[nc + cc];
-    double e = e_internal_at(G, X, P, 0, 0, 0);
-    double p = G.gm1 * rho * e;
-    Binv2 B = si_B(G, rho, p, dt, nf);
+    const double rho = X[cc];
+    const double E = X[nc + cc];
+    const double e = e_internal_at(G, X, P, 0, 0, 0);
+    const double p = G.gm1 * rho * e;
+    const double th = G.theta;
+    const double bpp = th * th * dt * G.gamma * p;
+    double rl[ND], den[3 + ND], inv[3 + ND];
+    den[0] = rho;
+    den[1] = e;
+    den[2] = bpp;
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+        int o[3] = {0, 0, 0};
+        o[c] = -1;
+        rl[c] = load_cell(G, X, P, o[0], o[1], o[2]);
+        den[3 + c] = 0.5 * (rl[c] + rho);           // rho_f on the lower face
+    }
+    recip_all<3 + ND>(den, inv);
+    const double irho = inv[0], ie = inv[1], ibpp = inv[2];
+    double b00, b01, b10, b11;
+    if (nf == 2) {
+        const double bpe = th * G.gm1;
+        const double bep = th * th * dt * p * irho;
+        const double bee = th * irho;
+        const double idet = 1.0 / (bpp * bee - bpe * bep);
+        b00 = bee * idet;
+        b01 = -bpe * idet;
+        b10 = -bep * idet;
+        b11 = bpp * idet;
+    } else {
+        b00 = ibpp;
+        b01 = b10 = b11 = 0.0;
+    }
     const long long mi = mg0(G, P);
     if (nf == 1) {
-        M[mi] = (T)((1.0 / dt) / B.bpp);
+        M[mi] = (T)(idt * ibpp);
     } else {
-        M[0 * nc + mi] = (T)(B.b00 / dt);
-        M[1 * nc + mi] = (T)(B.b01 / dt);
-        M[2 * nc + mi] = (T)(B.b10 / dt);
-        M[3 * nc + mi] = (T)(B.b11 / dt);
+        M[0 * nc + mi] = (T)(b00 * idt);
+        M[1 * nc + mi] = (T)(b01 * idt);
+        M[2 * nc + mi] = (T)(b10 * idt);
+        M[3 * nc + mi] = (T)(b11 * idt);
     }
-    const double cv = 1.0 / G.gm1;
     const double chi0 = (G.has_cond) ? conductivity_si(G, G.gm1 * e) : 0.0;
-    double dpdrho = G.gm1 * e, dpde = G.gm1 * rho;
+    const double dpdrho = G.gm1 * e, dpde = G.gm1 * rho;
     C[PcLr * nc + cc] = (T)L[cc];
     C[PcLE * nc + cc] = (T)L[nc + cc];
-    C[PcInvRho * nc + cc] = (T)(1.0 / rho);
+    C[PcInvRho * nc + cc] = (T)irho;
     C[PcE * nc + cc] = (T)E;
     C[PcDpdrho * nc + cc] = (T)dpdrho;
     C[PcDpde * nc + cc] = (T)dpde;
-    C[PcInvDpdrho * nc + cc] = (T)(1.0 / dpdrho);
-    C[PcCde * nc + cc] = (T)(1.0 / (G.gamma * rho));
+    C[PcInvDpdrho * nc + cc] = (T)(G.igm1 * ie);
+    C[PcCde * nc + cc] = (T)(G.igamma * irho);
     // r_p = Pr r_rho + PE r_E - dpde <u.r_u>: first row of dV/dU in the
     // product form printed in Sect. 3.2 (no cancellation between terms)
-    const double Pr = dpdrho - dpde * E / rho, PE = dpde / rho;
+    const double Eir = E * irho;
+    const double Pr = dpdrho - dpde * Eir, PE = dpde * irho;
     C[PcPr * nc + cc] = (T)Pr;
     C[PcPE * nc + cc] = (T)PE;
     if (sizeof(T) == 8) {
-        if (nf == 1) {
-            C[PcQ0 * nc + cc] = (T)(1.0 / B.bpp);
-        } else {
-            C[PcQ0 * nc + cc] = (T)B.b00;
-            C[PcQ1 * nc + cc] = (T)B.b01;
-            C[PcQ2 * nc + cc] = (T)B.b10;
-            C[PcQ3 * nc + cc] = (T)B.b11;
+        C[PcQ0 * nc + cc] = (T)b00;
+        if (nf == 2) {
+            C[PcQ1 * nc + cc] = (T)b01;
+            C[PcQ2 * nc + cc] = (T)b10;
+            C[PcQ3 * nc + cc] = (T)b11;
         }
     } else {
-        // rhs = B^-1 (r_p, r_e) with r_e = (r_E - E r_rho)/rho - <u.r_u>
-        double b00, b01, b10, b11;
-        if (nf == 1) { b00 = 1.0 / B.bpp; b01 = 0.0; b10 = 0.0; b11 = 0.0; }
-        else { b00 = B.b00; b01 = B.b01; b10 = B.b10; b11 = B.b11; }
-        C[PcQ0 * nc + cc] = (T)(b00 * Pr - b01 * E / rho);
-        C[PcQ1 * nc + cc] = (T)(b00 * PE + b01 / rho);
+        // rhs = B^-1 (r_p, r_e) with r_e = (r_E - E r_rho)/rho - <u.r_u>,
+        // folded in double (no cancellation in FP32)
+        C[PcQ0 * nc + cc] = (T)(b00 * Pr - b01 * Eir);
+        C[PcQ1 * nc + cc] = (T)(b00 * PE + b01 * irho);
         C[PcQ2 * nc + cc] = (T)(b00 * dpde + b01);
-        C[PcQ3 * nc + cc] = (T)(b10 * Pr - b11 * E / rho);
-        C[PcQ4 * nc + cc] = (T)(b10 * PE + b11 / rho);
+        C[PcQ3 * nc + cc] = (T)(b10 * Pr - b11 * Eir);
+        C[PcQ4 * nc + cc] = (T)(b10 * PE + b11 * irho);
         C[PcQ5 * nc + cc] = (T)(b10 * dpde + b11);
     }
     C[PcRinvR * nc + cc] = (T)Rinv[cc];
@@ -185,20 +191,19 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
         const bool wall = is_wall_slot(G, c, P);
         int o[3] = {0, 0, 0};
         o[c] = -1;
-        double rl = load_cell(G, X, P, o[0], o[1], o[2]);
-        double rho_f = 0.5 * (rl + rho);
+        const double irhof = inv[3 + c];
         const double m = (wall || G.n[c] == 1) ? 0.0 : 1.0;
-        K[(0 * ND + c) * nc + mi] = (T)(m / rho_f);
+        K[(0 * ND + c) * nc + mi] = (T)(m * irhof);
         if (nf == 2) {
             double chil = 0.0;
             if (G.has_cond) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
-            K[(1 * ND + c) * nc + mi] = (T)(m * (0.5 * (chil + chi0)) / cv);
+            K[(1 * ND + c) * nc + mi] = (T)(m * (0.5 * (chil + chi0)) * G.gm1);
         }
         const double u = wall ? 0.0 : X[(2 + c) * nc + cc];
         C[(PcLu + c) * nc + cc] = (T)L[(2 + c) * nc + cc];
         C[(PcU + c) * nc + cc] = (T)u;
-        C[(PcInvRhof + c) * nc + cc] = (T)(wall ? 0.0 : 1.0 / rho_f);
-        C[(PcThf + c) * nc + cc] = (T)(wall ? 0.0 : G.theta * G.idx[c] / rho_f);
+        C[(PcInvRhof + c) * nc + cc] = (T)(wall ? 0.0 : irhof);
+        C[(PcThf + c) * nc + cc] = (T)(wall ? 0.0 : G.theta * G.idx[c] * irhof);
         C[(PcRinvU + c) * nc + cc] = (T)Rinv[(2 + c) * nc + cc];
     }
 }
@@ -214,7 +219,7 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
 template <typename T>
 void launch_pc_setup(const Grid& G, const double* X, const double* L, const double* Rinv, double dt, int nf, T* C,
                      MGLevel& L0, cudaStream_t s) {
-    CELL_LAUNCH_T(k_pc_setup, T, G, X, L, Rinv, dt, nf, C, (T*)L0.M, (T*)L0.K);
+    CELL_LAUNCH_T(k_pc_setup, T, G, X, L, Rinv, dt, 1.0 / dt, nf, C, (T*)L0.M, (T*)L0.K);
 }
 template void launch_pc_setup<double>(const Grid&, const double*, const double*, const double*, double, int, double*,
                                       MGLevel&, cudaStream_t);
@@ -616,47 +621,83 @@ void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t
 template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 
-// coarse parents of fine index i along a coarsened direction
-__device__ __forceinline__ void parents(int i, int nc, int bc, int& par, int& oth) {
-    par = i >> 1;
-    oth = (i & 1) ? par + 1 : par - 1;
-    if (bc == 0) oth = wrapi(oth, nc);
-    else if (oth < 0 || oth >= nc) oth = par;
-}
-
+// Cell-centred linear prolongation x_f += P x_c, one thread per coarse cell:
+// the thread loads the coarse neighbourhood once (3 values along each
+// coarsened direction) and updates its 2^k children.  A child at offset
+// delta along a coarsened direction interpolates 3/4 of its parent and 1/4
+// of the parent's neighbour on its side (periodic wrap; at a wall the parent
+// itself), along x, then y, then z.
 template <typename T, int NF, int ND>
 __global__ void k_prolong(int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
                           T* __restrict__ xf) {
-    int i[3];
+    int ic[3];
     long long cc;
-    if (!lvl_pos(F, i, cc)) return;
-    const bool cx = F.n[0] != C.n[0], cy = F.n[1] != C.n[1], cz = F.n[2] != C.n[2];
-    int px = i[0], ox = i[0], py = i[1], oy = i[1], pz = i[2], oz = i[2];
-    if (cx) parents(i[0], C.n[0], bc0, px, ox);
-    if (cy) parents(i[1], C.n[1], bc1, py, oy);
-    if (cz) parents(i[2], C.n[2], bc2, pz, oz);
+    if (!lvl_pos(C, ic, cc)) return;
+    const bool cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
+    const int bc[3] = {bc0, bc1, bc2};
+    // coarse indices at offsets -1, 0, +1 along each direction
+    int nb[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int i = ic[d], n = C.n[d];
+        nb[d][1] = i;
+        if (!cd[d]) {
+            nb[d][0] = nb[d][2] = i;
+        } else if (bc[d] == 0) {
+            nb[d][0] = wrapi(i - 1, n);
+            nb[d][2] = wrapi(i + 1, n);
+        } else {
+            nb[d][0] = i - 1 < 0 ? i : i - 1;
+            nb[d][2] = i + 1 >= n ? i : i + 1;
+        }
+    }
     const T w0 = (T)0.75, w1 = (T)0.25;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const T* q = xc + (long long)f * C.nc;
-        // interpolate along x, then y, then z (the oracle's order)
-        auto along_x = [&](int yy, int zz) -> T {
-            T a = q[lflat(C, px, yy, zz)];
-            return cx ? w0 * a + w1 * q[lflat(C, ox, yy, zz)] : a;
-        };
-        auto along_y = [&](int zz) -> T {
-            T a = along_x(py, zz);
-            return cy ? w0 * a + w1 * along_x(oy, zz) : a;
-        };
-        T a = along_y(pz);
-        T v = cz ? w0 * a + w1 * along_y(oz) : a;
-        xf[(long long)f * F.nc + cc] = xf[(long long)f * F.nc + cc] + v;
+        T* out = xf + (long long)f * F.nc;
+        T v[3][3][3];       // v[z][y][x], offsets -1..+1 (only 0 along a direction not coarsened)
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx)
+                    v[kz][ky][kx] = q[lflat(C, nb[0][kx], nb[1][ky], nb[2][kz])];
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+            if (dz && !cd[2]) continue;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                if (dy && !cd[1]) continue;
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    if (dx && !cd[0]) continue;
+                    // the other parent lies at offset -1 for child 0 and +1 for child 1
+                    auto along_x = [&](int yy, int zz) -> T {
+                        const T a = v[zz][yy][1], o = dx ? v[zz][yy][2] : v[zz][yy][0];
+                        return cd[0] ? w0 * a + w1 * o : a;
+                    };
+                    auto along_y = [&](int zz) -> T {
+                        const T a = along_x(1, zz), o = dy ? along_x(2, zz) : along_x(0, zz);
+                        return cd[1] ? w0 * a + w1 * o : a;
+                    };
+                    const T a = along_y(1), o = dz ? along_y(2) : along_y(0);
+                    const T val = cd[2] ? w0 * a + w1 * o : a;
+                    const int fx = cd[0] ? 2 * ic[0] + dx : ic[0];
+                    const int fy = cd[1] ? 2 * ic[1] + dy : ic[1];
+                    const int fz = cd[2] ? 2 * ic[2] + dz : ic[2];
+                    const long long j = lflat(F, fx, fy, fz);
+                    out[j] = out[j] + val;
+                }
+            }
+        }
     }
 }
 
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
-    CellLaunch cl = cell_launch(F.n);
+    CellLaunch cl = cell_launch(C.n);
     MG_DISPATCH(k_prolong, cl.grid, cl.block, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C), (const T*)C.x, (T*)F.x);
 }
 template void launch_prolong<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);

@@ -324,11 +324,12 @@ __global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, d
     if (cell_pos(G.n, P, cc)) {
         const long long nc = G.ncell;
         double rho = X[cc], E = X[nc + cc];
-        double Lv[5], Rv[5];
+        double Lv[2 + ND], Rv[2 + ND];
         Lv[0] = rho; Rv[0] = rho;
         Lv[1] = rho * E; Rv[1] = E;
         double e0 = internal_e(G, X, P, 0, 0, 0);
         double cs0 = sqrt(G.gamma * G.gm1 * e0);
+#pragma unroll
         for (int c = 0; c < ND; ++c) {
             if (is_wall_slot(G, c, P)) { Lv[2 + c] = 1.0; Rv[2 + c] = 1.0; continue; }
             int o[3] = {0, 0, 0};
@@ -342,13 +343,22 @@ __global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, d
             Lv[2 + c] = rho_f * fmax(au, alpha1 * cs_f);
             Rv[2 + c] = fmax(au, alpha2 * cs_f);
         }
+        // all 2(2+ND) reciprocals with one division
+        double den[2 * (2 + ND)], inv[2 * (2 + ND)];
+#pragma unroll
+        for (int k = 0; k < 2 + ND; ++k) {
+            den[k] = Lv[k];
+            den[2 + ND + k] = Rv[k];
+        }
+        recip_all<2 * (2 + ND)>(den, inv);
+#pragma unroll
         for (int k = 0; k < 2 + ND; ++k) {
             long long j = k * nc + cc;
             L[j] = Lv[k];
             R[j] = Rv[k];
-            Linv[j] = 1.0 / Lv[k];
-            Rinv[j] = 1.0 / Rv[k];
-            double xh = X[j] / Rv[k];
+            Linv[j] = inv[k];
+            Rinv[j] = inv[2 + ND + k];
+            double xh = X[j] * inv[2 + ND + k];
             if (k >= 2 && is_wall_slot(G, k - 2, P)) xh = 0.0;
             acc += xh * xh;
         }

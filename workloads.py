@@ -42,6 +42,13 @@ problems stand in for them, following the paper's test problems of Sect. 5.1):
 5. Problem 2's construction at 128^2 (and 8x8), CFL_hydro = 50, 4 steps, used
    for the adjoint.
 
+Study workload (no noise): the 3D Taylor-Green vortex of the paper's
+Sect. 5.1.3 on [0, 2 pi]^3 (L = 1), 64^3 periodic, gamma = 7/5, rho_0 = 1,
+u_0 = 1, u_x = sin x cos y cos z, u_y = -cos x sin y cos z, u_z = 0 sampled at
+the face centres, p = p_0 + (2 + cos 2z)(cos 2x + cos 2y)/16 at the cell
+centres with p_0 = 1/(gamma M_s^2); Crank-Nicolson, sound-wave
+preconditioner.
+
 Seeds: numpy.random.default_rng(problem number); the 8x8 adjoint case uses 50.
 """
 from __future__ import annotations
@@ -279,6 +286,30 @@ def make_vortex(n, ndim, seed, mach, cfl, n_steps, theta, gamma=5.0 / 3.0, noise
     return Workload(name=name, ndim=ndim, n=tuple(n), lo=lo, hi=hi, bc=bc, gamma=gamma,
                     g=(0.0, 0.0, 0.0), K0=0.0, chi_exp=3.0, energy_form=energy_form, X0=X0,
                     theta=theta, cfl_hydro=cfl, n_steps=n_steps, precond=precond, seed=seed)
+
+
+def make_tgv(n: int = 64, mach: float = 1e-1, gamma: float = 1.4) -> Workload:
+    """The Taylor-Green vortex of the module docstring on an n^3 grid; Mach
+    number M_s = u_0 / c_s with c_s = sqrt(gamma p_0 / rho_0)."""
+    lo = (0.0, 0.0, 0.0)
+    hi = (2.0 * math.pi,) * 3
+    bc = (BC_PERIODIC,) * 3
+    xc, yc, zc = (_centres(n, lo[d], hi[d]) for d in range(3))
+    xf, yf = _faces(n, lo[0], hi[0]), _faces(n, lo[1], hi[1])
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    p0 = 1.0 / (gamma * mach * mach)
+    p = p0 + (2.0 + np.cos(2.0 * Z)) * (np.cos(2.0 * X) + np.cos(2.0 * Y)) / 16.0
+    rho = np.ones_like(p)
+    e = p / ((gamma - 1.0) * rho)
+    Zx, Yx, Xx = np.meshgrid(zc, yc, xf, indexing="ij")     # x-faces
+    ux = np.sin(Xx) * np.cos(Yx) * np.cos(Zx)
+    Zy, Yy, Xy = np.meshgrid(zc, yf, xc, indexing="ij")     # y-faces
+    uy = -np.cos(Xy) * np.sin(Yy) * np.cos(Zy)
+    uz = np.zeros_like(p)
+    X0 = _pack([rho, e, ux, uy, uz])
+    return Workload(name="tgv3d", ndim=3, n=(n, n, n), lo=lo, hi=hi, bc=bc, gamma=gamma, g=(0.0, 0.0, 0.0),
+                    K0=0.0, chi_exp=3.0, energy_form=ENERGY_INTERNAL, X0=X0, theta=0.5, cfl_hydro=1.0,
+                    n_steps=100, precond=PRECOND_SOUND, seed=0)
 
 
 def config(cid: int, n: Optional[Sequence[int]] = None, mach: Optional[float] = None,
