@@ -170,6 +170,9 @@ def make_workload(n):
 # (problem 2 at 32^2 and CFL 100) one cycle is not enough, hence the
 # library default.  Command-line options override these.
 OPT_OVERRIDES = {"mg_cycles": 1}
+# the options given on the command line alone (the studies otherwise use the
+# library defaults)
+CLI_OPTS = {}
 
 
 def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
@@ -303,6 +306,218 @@ def kernel_main(args):
                       "gcell_s": wl.ncell / (ms / 1e3) / 1e9}))
 
 
+# Taylor-Green vortex 64^3 (Sect. 5.1.2), the paper's Table 1 (implicit
+# columns: CFL_hydro, CFL_adv, Newton per step, GMRES per Newton, parabolic
+# iterations per GMRES) and Table 2 (time and value of the peak kinetic
+# energy decay rate), for comparison beside this solver's figures.
+TGV_TABLE1 = {1e-1: (7.1, 0.5, 3.8, 16.6, 2.4), 1e-2: (70.0, 0.5, 3.1, 15.4, 2.5),
+              1e-3: (820.0, 0.5, 2.7, 16.2, 2.5), 1e-4: (1.1e4, 0.5, 2.0, 16.1, 2.8),
+              1e-5: (8.1e4, 0.5, 2.0, 22.2, 2.9), 1e-6: (4.9e5, 0.49, 4.5, 291.5, 3.0)}
+TGV_TABLE2 = {1e-1: (8.1656, 1.2504e-2), 1e-2: (8.1695, 1.2496e-2), 1e-3: (8.1695, 1.2496e-2),
+              1e-4: (8.1696, 1.2496e-2), 1e-5: (8.1695, 1.2498e-2), 1e-6: (8.1681, 1.2520e-2)}
+
+
+def tgv_speed_max(X, nc):
+    """max over cells of |u| with u the cell mean of the face velocities."""
+    import torch
+    n = round(nc ** (1.0 / 3.0))
+    sq = 0.0
+    for d in range(3):
+        u = X[(2 + d) * nc:(3 + d) * nc].reshape(n, n, n)
+        ub = 0.5 * (u + torch.roll(u, -1, dims=2 - d))
+        sq = sq + ub * ub
+    return float(sq.sqrt().max())
+
+
+def tgv_kinetic_energy(X, nc):
+    """Volume mean of rho_f u_f^2 / 2 summed over the face velocities."""
+    import torch
+    n = round(nc ** (1.0 / 3.0))
+    rho = X[:nc].reshape(n, n, n)
+    ke = 0.0
+    for d in range(3):
+        u = X[(2 + d) * nc:(3 + d) * nc].reshape(n, n, n)
+        rf = 0.5 * (rho + torch.roll(rho, 1, dims=2 - d))
+        ke = ke + float((0.5 * rf * u * u).mean())
+    return ke
+
+
+def study_tgv(args):
+    """--study tgv: the Taylor-Green runs of Sect. 5.1.2 at 64^3.  For each
+    Mach number: 100 steps at CFL_hydro = 1 to let the initial acoustic
+    transient pass (as in the paper), then --steps steps at CFL_adv = 0.5
+    (and 0.05 for M = 1e-6), reporting Newton iterations per step, GMRES
+    iterations per Newton iteration and the simulated time per wall-clock
+    second.  --decay adds a run from t = 0 to t = 20 at CFL_adv = 0.5 with
+    the peak of the kinetic energy decay rate; --sweep adds GMRES iterations
+    against CFL_hydro with and without the preconditioner (alpha1 = 1
+    without, as in the paper's Fig. tgv)."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    import workloads as W
+    prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
+    n = args.study_n
+    h = 2.0 * math.pi / n
+    machs = [float(m) for m in args.machs.split(",")]
+
+    def solver(wl, **kw):
+        o = jf.default_options(**{"theta": wl.theta, "precond": wl.precond, "precision": prec, **CLI_OPTS, **kw})
+        return jf.Solver.from_workload(wl, o)
+
+    def run(S, X, dt, steps, tol=NEWTON_TOL):
+        """steps implicit steps; stops at the first step that fails (error
+        status), whose message is returned beside the statistics"""
+        stats, err = [], None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            try:
+                stats.append(S.step(X, dt, tol, ETA))
+            except jf.JFNKError as e:
+                err = str(e)
+                break
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, stats, err
+
+    def summary(stats, err=None):
+        if not stats:
+            return {"steps_done": 0, "error": err}
+        nn = sum(s["newton_iterations"] for s in stats)
+        its = [g for s in stats for g in s["gmres_iterations"]]
+        return {"newton_per_step": nn / len(stats), "gmres_per_newton": sum(its) / max(1, nn),
+                "gmres_min": min(its), "gmres_max": max(its),
+                "unconverged_linear_solves": sum(1 - c for s in stats for c in s["gmres_converged"]),
+                "steps_converged": sum(1 for s in stats if s["converged"]), "steps_done": len(stats),
+                "error": err}
+
+    for mach in machs:
+        wl = W.make_tgv(n, mach)
+        S = solver(wl)
+        X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+        _, _, err = run(S, X, S.dt_from_cfl(X, 1.0), 100)
+        if err:
+            print(json.dumps({"study": "tgv", "mach": mach, "transient_error": err}), flush=True)
+            continue
+        Xt = X.clone()
+        cs = 1.0 / mach          # background sound speed sqrt(gamma p_0 / rho_0) = u_0 / M_s
+        for cfl_adv in ([0.5, 0.05] if mach <= 1e-6 else [0.5]):
+            X.copy_(Xt)
+            dt = cfl_adv * h / tgv_speed_max(X, wl.ncell)
+            el, stats, err = run(S, X, dt, args.steps)
+            done = max(1, len(stats))
+            line = {"study": "tgv", "mach": mach, "n": n, "precision": args.precision, "cfl_adv": cfl_adv,
+                    "cfl_hydro": dt * (tgv_speed_max(Xt, wl.ncell) + cs) / h, "dt": dt, "steps": args.steps,
+                    "steps_per_s": done / el, "sim_time_per_s": done * dt / el,
+                    "vcycles_per_gmres": S.options.mg_cycles, **summary(stats, err)}
+            if cfl_adv == 0.5 and mach in TGV_TABLE1:
+                line["paper_table1"] = dict(zip(["cfl_hydro", "cfl_adv", "newton_per_step", "gmres_per_newton",
+                                                 "parabolic_per_gmres"], TGV_TABLE1[mach]))
+            print(json.dumps(line), flush=True)
+        if args.sweep:
+            for cfl in (0.1, 1.0, 10.0, 100.0, 1e3, 1e4, 1e5):
+                if cfl * mach > 1.0:     # CFL_adv ~ CFL_hydro M_s > 1: the SI scheme is unstable there
+                    continue
+                res = {"study": "tgv_sweep", "mach": mach, "cfl_hydro": cfl}
+                for tag, kw in (("pbp", {}), ("none_alpha1", {"precond": 0, "alpha1": 1.0})):
+                    S2 = solver(wl, **kw) if kw else S
+                    X.copy_(Xt)
+                    dt = S2.dt_from_cfl(X, cfl)
+                    el, stats, err = run(S2, X, dt, 5)
+                    res[tag] = summary(stats, err)
+                print(json.dumps(res), flush=True)
+        if args.decay:
+            X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+            dt = 0.5 * h / tgv_speed_max(X, wl.ncell)
+            nsteps = int(math.ceil(20.0 / dt))
+            ke = [tgv_kinetic_energy(X, wl.ncell)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its, err = 0, None
+            for _ in range(nsteps):
+                try:
+                    st = S.step(X, dt, NEWTON_TOL, ETA)
+                except jf.JFNKError as e:
+                    err = str(e)
+                    break
+                its += st["gmres_iterations_total"]
+                ke.append(tgv_kinetic_energy(X, wl.ncell))
+            el = time.perf_counter() - t0
+            if err or len(ke) < 3:
+                print(json.dumps({"study": "tgv_decay", "mach": mach, "error": err, "steps_done": len(ke) - 1}),
+                      flush=True)
+                continue
+            rate = [-(ke[k + 1] - ke[k - 1]) / (2 * dt) for k in range(1, len(ke) - 1)]
+            k = max(range(len(rate)), key=lambda i: rate[i])
+            line = {"study": "tgv_decay", "mach": mach, "dt": dt, "steps": nsteps, "wall_s": el,
+                    "ke0": ke[0], "ke_end": ke[-1], "t_peak": (k + 1) * dt, "rate_peak": rate[k],
+                    "gmres_total": its}
+            if mach in TGV_TABLE2:
+                line["paper_table2"] = {"t_peak": TGV_TABLE2[mach][0], "rate_peak": TGV_TABLE2[mach][1]}
+            print(json.dumps(line), flush=True)
+
+
+def study_vortex(args):
+    """--study vortex: the advected isentropic vortex of Sects. 3.7 and 5.1.1
+    at 64^2, advected to t = 0.4 at T_inf = 1, 1e2, 1e6, 1e10 (Mach 1e-1 ...
+    1e-6) for a range of advective CFL numbers, with the JFNK+PBP step
+    (Crank-Nicolson) and with the SI scheme as a time integrator (one SI
+    solve per step, theta = 1).  Reports the L1, L2 and Linf errors of the
+    velocity along the advection against the shifted initial field, as the
+    paper defines them."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    import workloads as W
+    prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
+    n, t_end = 64, 0.4
+    dx = 8.0 / n
+    for T_inf in (1.0, 1e2, 1e6, 1e10):
+        wl = W.make_isentropic_vortex(n, T_inf)
+        nc = wl.ncell
+        u_exact = torch.as_tensor(W.make_isentropic_vortex(n, T_inf, x_shift=t_end).X0[2 * nc:3 * nc],
+                                  device="cuda")
+        mach = 0.75 / (2.0 * math.pi * math.sqrt(wl.gamma * T_inf))
+        for cfl_adv in (0.01, 0.03, 0.1, 0.3, 1.0, 3.0):
+            nsteps = max(1, round(t_end / (cfl_adv * dx)))
+            dt = t_end / nsteps
+            for arm in ("jfnk", "si"):
+                theta = 0.5 if arm == "jfnk" else 1.0
+                o = jf.default_options(**{"theta": theta, "precond": 1, "precision": prec, **CLI_OPTS})
+                S = jf.Solver.from_workload(wl, o)
+                X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+                err, newton, gmres = None, 0, 0
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(nsteps):
+                    try:
+                        if arm == "jfnk":
+                            st = S.step(X, dt, NEWTON_TOL, ETA)
+                            newton += st["newton_iterations"]
+                            gmres += st["gmres_iterations_total"]
+                        else:
+                            S.si_step(X, dt)
+                    except jf.JFNKError as e:
+                        err = str(e)
+                        break
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                d = X[2 * nc:3 * nc] - u_exact
+                ok = err is None and bool(torch.isfinite(d).all())
+                line = {"study": "vortex", "arm": arm, "T_inf": T_inf, "mach": mach, "cfl_adv": cfl_adv,
+                        "cfl_hydro": dt * (1.0 + math.sqrt(wl.gamma * T_inf)) / dx, "steps": nsteps, "wall_s": el,
+                        "L1": float(d.abs().mean()) if ok else None,
+                        "L2": float(d.pow(2).mean().sqrt()) if ok else None,
+                        "Linf": float(d.abs().max()) if ok else None, "error": err if err else (None if ok else
+                                                                                          "non-finite state")}
+                if arm == "jfnk":
+                    line["newton_per_step"] = newton / nsteps
+                    line["gmres_per_newton"] = gmres / max(1, newton)
+                print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,10 +536,24 @@ def main():
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
+    ap.add_argument("--study", choices=["tgv", "vortex"], default=None,
+                    help="tgv: the Taylor-Green iteration and decay study of Sect. 5.1.2; vortex: the "
+                         "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1 (JSON lines)")
+    ap.add_argument("--machs", default="1e-1,1e-2,1e-3,1e-4,1e-5,1e-6", help="Mach numbers of --study tgv")
+    ap.add_argument("--decay", action="store_true", help="--study tgv: decay run to t = 20")
+    ap.add_argument("--study-n", type=int, default=64, help="cells per direction of --study tgv")
+    ap.add_argument("--sweep", action="store_true", help="--study tgv: GMRES iterations against CFL_hydro")
     args = ap.parse_args()
     for k in ("mg_cycles", "mg_nu1", "mg_nu2", "pc_freeze"):
         if getattr(args, k) is not None:
             OPT_OVERRIDES[k] = getattr(args, k)
+            CLI_OPTS[k] = getattr(args, k)
+    if args.study == "tgv":
+        study_tgv(args)
+        return
+    if args.study == "vortex":
+        study_vortex(args)
+        return
     if args.only:
         kernel_main(args)
         return

@@ -168,6 +168,16 @@ jfnk_status jfnk_jv(jfnk_handle* h, const double* X, double dt, const void* v, v
  * fixed multigrid V-cycles of the options.  v, w: precision type. */
 jfnk_status jfnk_precond_apply(jfnk_handle* h, const double* X, double dt, const void* v, void* w);
 
+/* One step of the semi-implicit scheme used as a time integrator (Sect.
+ * 3.6): F_U(X^n) = -R_U(X^n) is transformed to the primitive variables, the
+ * SI system built at X^n is solved once (the multigrid of the options), the
+ * correction is transformed back and added: X^{n+1} = X^n + dX, in place in
+ * X.  First order in time and stable only for advective CFL numbers well
+ * below one (Sect. 3.7); theta = 1 gives the paper's scheme (backward Euler
+ * in the SI terms).  Needs precond 1 or 2 (JFNK_EINVAL otherwise).
+ * Asynchronous on the bound stream; non-finite values are not checked. */
+jfnk_status jfnk_si_step(jfnk_handle* h, double* X, double dt);
+
 /* One Newton linear solve (Eq. jacobian_system_norm with right
  * preconditioning, Eqs. lin_sys_rp, lin_sys_rp2, stopping rule Eq.
  * forcing_term): given the iterate X and X^n, returns the scaled correction

@@ -265,3 +265,20 @@ def newton_step(P: D.Problem, Xn, dt: float, opts: Options, on_iterate=None):
             st.converged = True
             break
     return X, st
+
+
+def si_step(P: D.Problem, Xn, dt: float, opts: Options) -> torch.Tensor:
+    """One step of the SI scheme used as a time integrator (Sect. 3.6):
+    F_U(X^n) = -R_U(X^n); transform to the primitive residual, solve the SI
+    system built at X^n, transform back and add: X^{n+1} = X^n + dX.  In the
+    scaled variables of the preconditioner, dX = R M^-1(-F^) with the
+    preconditioner of Sect. 4.3 (its sign convention makes M approximate
+    +dF/dX).  First order in time; the paper's scheme treats the SI terms by
+    backward Euler (theta = 1)."""
+    from . import precond as PC
+    Xn = D.as_tensor(Xn)
+    sc = scaling(P, Xn, opts)
+    F = D.residual(P, Xn, Xn, dt)                      # G(X^n) - b^n(X^n) = -R_U(X^n)
+    si = PC.setup(P, Xn, dt, opts)
+    dxh = PC.apply(si, -F / sc.L, sc)
+    return Xn + sc.R * dxh

@@ -110,6 +110,7 @@ def lib():
             "jfnk_set_profiling": (I, [P, I]),
             "jfnk_residual_noalloc": (I, [P, P, P, D, P]),
             "jfnk_vjp_residual": (I, [P, P, D, P, P]),
+            "jfnk_si_step": (I, [P, P, D]),
             "jfnk_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(jfnk_stats)]),
             "jfnk_last_error": (ctypes.c_char_p, [P]),
             "jfnk_destroy": (None, [P]),
@@ -125,7 +126,7 @@ def lib():
 EXPORTED = ["jfnk_default_options", "jfnk_create", "jfnk_workspace_bytes", "jfnk_bind", "jfnk_vector_length",
             "jfnk_set_options", "jfnk_residual", "jfnk_scaling", "jfnk_jv", "jfnk_precond_apply",
             "jfnk_linear_solve", "jfnk_step", "jfnk_dt_from_cfl", "jfnk_set_profiling", "jfnk_last_error",
-            "jfnk_destroy", "jfnk_residual_noalloc", "jfnk_vjp_residual", "jfnk_vjp"]
+            "jfnk_destroy", "jfnk_residual_noalloc", "jfnk_vjp_residual", "jfnk_vjp", "jfnk_si_step"]
 
 
 class JFNKError(RuntimeError):
@@ -264,6 +265,11 @@ class Solver:
         d = st.as_dict()
         d["status"] = code
         return d
+
+    def si_step(self, X: torch.Tensor, dt: float) -> None:
+        """jfnk_si_step: one step of the semi-implicit scheme as a time
+        integrator, in place in X."""
+        self._check(lib().jfnk_si_step(self.h, _ptr(X), dt))
 
     def vjp_residual(self, X: torch.Tensor, dt: float, w: torch.Tensor) -> torch.Tensor:
         """jfnk_vjp_residual: (dG/dX)^T w at X."""

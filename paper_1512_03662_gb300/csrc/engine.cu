@@ -422,6 +422,17 @@ jfnk_status newton_solve(jfnk_handle* h, const double* X, double dt, double eta,
     return gmres<T>(h, X, dt, eta, so);
 }
 
+// one step of the SI scheme as a time integrator (Sect. 3.6), in place in X
+template <typename T>
+void si_step(jfnk_handle* h, double* X, double dt) {
+    cudaStream_t s = h->stream;
+    eval<kModeBn, double>(h, X, dt, h->bn, (double*)nullptr);     // b^n at X^n
+    linearize<T>(h, X, dt, true);          // scaling, V[0] = -F^ = L^-1 R_U(X^n), SI setup at X^n
+    precond<T>(h, X, dt, Vcol<T>(h, 0), -1, Zcol<T>(h, 0));
+    launch_scale_copy<T, double>(Zcol<T>(h, 0), 1.0, nullptr, -1, 0, h->dxh, h->nvec, s);
+    launch_newton_update(X, h->R, h->dxh, h->nvec, h->partials, s);
+}
+
 // ---------------------------------------------------------------------------
 // adjoint (FP64 handles)
 // ---------------------------------------------------------------------------
@@ -805,6 +816,17 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
     S->kernel_launches = g_launch_count - launches0;
     if (!S->converged && !h->opt.fixed_iterations) return JFNK_ENOCONV_NEWTON;
     (void)gmres_fail;
+    return JFNK_OK;
+}
+
+jfnk_status jfnk_si_step(jfnk_handle* h, double* X, double dt) {
+    jfnk_status st = check_bound(h);
+    if (st) return st;
+    if (!X || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_si_step");
+    if (h->nf == 0) return fail(h, JFNK_EINVAL, "jfnk_si_step needs the SI preconditioner (precond 1 or 2)");
+    if (h->mixed) si_step<float>(h, X, dt);
+    else si_step<double>(h, X, dt);
+    CUDA_TRY(h, cudaGetLastError());
     return JFNK_OK;
 }
 

@@ -285,6 +285,80 @@ def test_mixed_precision_step_error(jf, cid, n):
     assert err < 1e-6, err
 
 
+@pytest.mark.parametrize("mach", [1e-1, 1e-4])
+def test_taylor_green_parity(jf, mach):
+    """The Taylor-Green study workload (gamma = 7/5, 2 pi periodic box) at
+    16^3: residual, Jv, preconditioner and a fixed-iteration step."""
+    wl = W.make_tgv(16, mach)
+    P = D.Problem.from_workload(wl)
+    Xn = torch.as_tensor(wl.X0)
+    rng = np.random.default_rng(3)
+    X = Xn * (1.0 + 1e-3 * torch.as_tensor(rng.uniform(-1, 1, Xn.shape)))
+    dt = D.cfl_dt(P, Xn, 1.0 / mach)          # CFL_adv about 1
+    S = _solver(jf, wl, lam=1e-4)
+    sc = J.scaling(P, X, J.Options())
+    assert _relnorm(S.residual(_dev(X), _dev(Xn), dt), D.residual(P, X, Xn, dt), sc.L) < 1e-10
+    v = torch.as_tensor(W.random_vector(wl, 3))
+    Jv, _ = S.jv(_dev(X), dt, _dev(v))
+    oo = J.Options(lam=1e-4)
+    Jo, _ = J.jv(P, X, D.G_operator(P, X, dt), J.scaling(P, X, oo), v, dt, oo)
+    assert _relnorm(Jv, Jo) < 1e-10
+    w = S.precond_apply(_dev(X), dt, _dev(v))
+    wo = PC.apply(PC.setup(P, X, dt, oo), v, J.scaling(P, X, oo))
+    assert _relnorm(w, wo) < 1e-10
+    # the fixed-iteration step at CFL_hydro = 10: at CFL_adv ~ 1 ten unconverged
+    # GMRES iterations amplify round-off differences beyond the step tolerance
+    dts = D.cfl_dt(P, Xn, 10.0)
+    o = jf.default_options(theta=wl.theta, precond=1, gmres_m=10, gmres_max_it=10, newton_max=2,
+                           fixed_iterations=1, lam=1e-4)
+    S2 = jf.Solver.from_workload(wl, o)
+    Xg = _dev(Xn)
+    S2.step(Xg, dts)
+    Xo, _ = J.newton_step(P, Xn, dts, J.Options(precond=1, gmres_m=10, gmres_max_it=10, newton_max=2,
+                                                 fixed_iterations=True, lam=1e-4))
+    # the pressure gradient cancels p_0 ~ 1/M^2 against dynamic pressures ~ 1,
+    # so round-off differences in F are ~ eps / M^2 relative (1e-8 at M = 1e-4),
+    # and the unconverged GMRES iterations amplify them: the bar scales with 1/M^2
+    tol = max(1e-8, 1e-14 / mach ** 2)
+    err = _relnorm(Xg - _dev(Xn), Xo - Xn, J.scaling(P, Xn, J.Options()).R)
+    assert err < tol, (err, tol)
+
+
+@pytest.mark.parametrize("cid,n,form,pc", PC_CASES)
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_si_step_parity(jf, cid, n, form, pc, theta):
+    """One step of the SI scheme as a time integrator (Sect. 3.6) against
+    the oracle's si_step (FP64, fixed multigrid cycles)."""
+    wl, P, X, Xn, dt = _case(cid, n, form)
+    P.theta = theta
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=theta, precond=pc))
+    Xg = _dev(X)
+    S.si_step(Xg, dt)
+    Xo = J.si_step(P, X, dt, J.Options(precond=pc))
+    sc = J.scaling(P, X, J.Options())
+    assert _relnorm(Xg - _dev(X), Xo - X, sc.R) < 1e-10
+
+
+def test_si_step_vortex_and_rejects_unpreconditioned(jf):
+    """The isentropic vortex of Sect. 3.7: ten SI steps at CFL_adv = 0.1
+    agree with the oracle's; a handle without preconditioner is refused."""
+    wl = W.make_isentropic_vortex(32, 1e2)
+    P = D.Problem.from_workload(wl, theta=1.0)
+    dt = 0.1 * (8.0 / 32)
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=1.0, precond=1))
+    Xg = _dev(wl.X0)
+    Xo = torch.as_tensor(wl.X0)
+    for _ in range(10):
+        S.si_step(Xg, dt)
+        Xo = J.si_step(P, Xo, dt, J.Options(precond=1))
+    sc = J.scaling(P, Xo, J.Options())
+    assert _relnorm(Xg - _dev(wl.X0), Xo - torch.as_tensor(wl.X0), sc.R) < 1e-10
+    S0 = jf.Solver.from_workload(wl, jf.default_options(theta=1.0, precond=0))
+    with pytest.raises(jf.JFNKError) as e:
+        S0.si_step(_dev(wl.X0), dt)
+    assert e.value.status == jf.JFNK_EINVAL
+
+
 @pytest.mark.parametrize("cid,n,form", CASES)
 def test_dt_from_cfl_parity(jf, cid, n, form):
     wl, P, X, Xn, dt = _case(cid, n, form)

@@ -256,7 +256,7 @@ def test_linear_sound_speed():
 
 
 def test_taylor_green_initial_tendency():
-    """Taylor-Green vortex of Sect. 5.1.3: at t = 0 the exact momentum
+    """Taylor-Green vortex of Sect. 5.1.2: at t = 0 the exact momentum
     equation gives, for rho = 1 and the stated pressure field,
     d_t u_x = -sin 2x cos 2z / 8, d_t u_y = -sin 2y cos 2z / 8,
     d_t u_z = sin 2z (cos 2x + cos 2y) / 8 (a divergence-free field, which

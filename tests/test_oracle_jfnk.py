@@ -332,3 +332,23 @@ def test_unpreconditioned_gmres_stalls_at_large_cfl():
     o = J.Options(precond=1, newton_max=1, newton_min=1)
     _, st = J.newton_step(P, X0, dt, o)
     assert st.gmres_iterations[0] < 30
+
+
+def test_si_step_reduces_to_forward_euler():
+    """As dt -> 0 the SI stepper of Sect. 3.6 becomes forward Euler in the
+    unknowns: (X^{n+1} - X^n)/dt -> (dU/dX)^-1 R_U(X^n), with an error of
+    order dt or smaller (the SI terms scale with dt).  Checked against a dense Jacobian
+    of U(X), with the exact inner solve so that only the scheme is tested."""
+    wl = W.config(1, n=(16, 16))
+    P = D.Problem.from_workload(wl)
+    P.theta = 1.0
+    X = torch.as_tensor(W.random_state(wl, 2, rel=0.05, vel=0.2))
+    JU = torch.func.jacrev(lambda x: D.pack(D.conserved(P, x)))(X)
+    target = torch.linalg.solve(JU, D.pack(D.rhs(P, X)))
+    errs = []
+    # at M = 0.01 the acoustic SI terms make the O(dt) term large: c dt/dx = 0.016 at dt = 1e-5
+    for dt in (1e-5, 1e-6):
+        X1 = J.si_step(P, X, dt, J.Options(precond=1, exact_inner=True))
+        errs.append(float(((X1 - X) / dt - target).norm() / target.norm()))
+    assert errs[1] < 3e-3, errs
+    assert errs[0] / errs[1] > 5.0, errs            # at least first order in dt

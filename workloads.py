@@ -42,8 +42,16 @@ problems stand in for them, following the paper's test problems of Sect. 5.1):
 5. Problem 2's construction at 128^2 (and 8x8), CFL_hydro = 50, 4 steps, used
    for the adjoint.
 
+Study workload (no noise): the advected isentropic vortex of the paper's
+Sect. 3.7 on [-4, 4]^2, periodic, gamma = 7/5, beta = 0.75, u_inf = 1:
+(du, dv) = beta/(2 pi) exp((1 - r^2)/2) (-y, x), dT = -(gamma-1) beta^2 /
+(8 gamma pi^2) exp(1 - r^2), rho = (T_inf + dT)^(1/(gamma-1)),
+e = T/(gamma-1) = rho^(gamma-1)/(gamma-1); T_inf = 1, 1e2, 1e6, 1e10 give
+M_s = beta/(2 pi sqrt(gamma T_inf)) = 1e-1 ... 1e-6 (rounded).  The exact
+solution at time t is the initial field shifted by u_inf t along x.
+
 Study workload (no noise): the 3D Taylor-Green vortex of the paper's
-Sect. 5.1.3 on [0, 2 pi]^3 (L = 1), 64^3 periodic, gamma = 7/5, rho_0 = 1,
+Sect. 5.1.2 on [0, 2 pi]^3 (L = 1), 64^3 periodic, gamma = 7/5, rho_0 = 1,
 u_0 = 1, u_x = sin x cos y cos z, u_y = -cos x sin y cos z, u_z = 0 sampled at
 the face centres, p = p_0 + (2 + cos 2z)(cos 2x + cos 2y)/16 at the cell
 centres with p_0 = 1/(gamma M_s^2); Crank-Nicolson, sound-wave
@@ -286,6 +294,41 @@ def make_vortex(n, ndim, seed, mach, cfl, n_steps, theta, gamma=5.0 / 3.0, noise
     return Workload(name=name, ndim=ndim, n=tuple(n), lo=lo, hi=hi, bc=bc, gamma=gamma,
                     g=(0.0, 0.0, 0.0), K0=0.0, chi_exp=3.0, energy_form=energy_form, X0=X0,
                     theta=theta, cfl_hydro=cfl, n_steps=n_steps, precond=precond, seed=seed)
+
+
+def make_isentropic_vortex(n: int = 64, T_inf: float = 1.0, x_shift: float = 0.0, beta: float = 0.75,
+                           gamma: float = 1.4, u_inf: float = 1.0) -> Workload:
+    """The advected isentropic vortex of the module docstring on an n^2 grid,
+    centred at (x_shift, 0) (periodic images included), so x_shift = u_inf t
+    gives the exact solution at time t."""
+    lo, hi = (-4.0, -4.0, 0.0), (4.0, 4.0, 1.0)
+    bc = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
+    L = hi[0] - lo[0]
+
+    def rel(x, y):
+        # position relative to the nearest image of the centre
+        dx = (x - x_shift - lo[0]) % L + lo[0]
+        return dx, y
+
+    xc, yc = _centres(n, lo[0], hi[0]), _centres(n, lo[1], hi[1])
+    xf, yf = _faces(n, lo[0], hi[0]), _faces(n, lo[1], hi[1])
+    Yc, Xc = np.meshgrid(yc, xc, indexing="ij")
+    x, y = rel(Xc, Yc)
+    dT = -(gamma - 1.0) * beta ** 2 / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - (x * x + y * y))
+    T = T_inf + dT
+    rho = T ** (1.0 / (gamma - 1.0))
+    e = T / (gamma - 1.0)
+    amp = beta / (2.0 * math.pi)
+    Yx, Xx = np.meshgrid(yc, xf, indexing="ij")           # x-faces
+    x, y = rel(Xx, Yx)
+    u = u_inf + amp * np.exp(0.5 * (1.0 - (x * x + y * y))) * (-y)
+    Yy, Xy = np.meshgrid(yf, xc, indexing="ij")           # y-faces
+    x, y = rel(Xy, Yy)
+    v = amp * np.exp(0.5 * (1.0 - (x * x + y * y))) * x
+    X0 = _pack([a[None] for a in (rho, e, u, v)])
+    return Workload(name="isentropic_vortex", ndim=2, n=(n, n, 1), lo=lo, hi=hi, bc=bc, gamma=gamma,
+                    g=(0.0, 0.0, 0.0), K0=0.0, chi_exp=3.0, energy_form=ENERGY_INTERNAL, X0=X0, theta=0.5,
+                    cfl_hydro=1.0, n_steps=1, precond=PRECOND_SOUND, seed=0)
 
 
 def make_tgv(n: int = 64, mach: float = 1e-1, gamma: float = 1.4) -> Workload:
