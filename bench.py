@@ -458,6 +458,46 @@ def study_tgv(args):
             print(json.dumps(line), flush=True)
 
 
+def vortex_run(jf, wl, u_exact, dt, nsteps, arm, prec, opts):
+    """Advect the isentropic vortex nsteps steps of dt with the JFNK+PBP step
+    (arm "jfnk") or the SI stepper (arm "si"); errors of u against u_exact
+    as the paper defines them (L1, L2: means over the grid; Linf: max)."""
+    import torch
+    nc = wl.ncell
+    theta = 0.5 if arm == "jfnk" else 1.0
+    o = jf.default_options(**{"theta": theta, "precond": 1, "precision": prec, **opts})
+    S = jf.Solver.from_workload(wl, o)
+    X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+    err, newton, gmres = None, 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        try:
+            if arm == "jfnk":
+                st = S.step(X, dt, o.newton_tol, o.eta)
+                newton += st["newton_iterations"]
+                gmres += st["gmres_iterations_total"]
+                if not st["converged"]:
+                    err = "Newton did not converge"
+                    break
+            else:
+                S.si_step(X, dt)
+        except jf.JFNKError as e:
+            err = str(e)
+            break
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    d = X[2 * nc:3 * nc] - u_exact
+    ok = err is None and bool(torch.isfinite(d).all())
+    r = {"wall_s": el, "L1": float(d.abs().mean()) if ok else None,
+         "L2": float(d.pow(2).mean().sqrt()) if ok else None, "Linf": float(d.abs().max()) if ok else None,
+         "error": err if err else (None if ok else "non-finite state")}
+    if arm == "jfnk":
+        r["newton_per_step"] = newton / nsteps
+        r["gmres_per_newton"] = gmres / max(1, newton)
+    return r
+
+
 def study_vortex(args):
     """--study vortex: the advected isentropic vortex of Sects. 3.7 and 5.1.1
     at 64^2, advected to t = 0.4 at T_inf = 1, 1e2, 1e6, 1e10 (Mach 1e-1 ...
@@ -465,7 +505,10 @@ def study_vortex(args):
     (Crank-Nicolson) and with the SI scheme as a time integrator (one SI
     solve per step, theta = 1).  Reports the L1, L2 and Linf errors of the
     velocity along the advection against the shifted initial field, as the
-    paper defines them."""
+    paper defines them.
+    --study params: the JFNK+PBP free parameters of Sect. 5.1.1 (perturbation
+    formula and lambda, alpha1, eta) on the same vortex at CFL_adv = 0.3 and
+    1, for M = 1e-1, 1e-4, 1e-6."""
     import torch
     from paper_1512_03662_gb300 import build as B
     B.build()
@@ -474,48 +517,32 @@ def study_vortex(args):
     prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
     n, t_end = 64, 0.4
     dx = 8.0 / n
-    for T_inf in (1.0, 1e2, 1e6, 1e10):
+    if args.study == "vortex":
+        T_list, cfls = (1.0, 1e2, 1e6, 1e10), (0.01, 0.03, 0.1, 0.3, 1.0, 3.0)
+        cases = [("jfnk", "default", {}), ("si", "default", {})]
+    else:
+        T_list, cfls = (1.0, 1e6, 1e10), (0.3, 1.0)
+        cases = [("jfnk", "pert_old lambda 1e-7 (default)", {}),
+                 ("jfnk", "pert_old lambda 1e-6", {"lam": 1e-6}),
+                 ("jfnk", "pert_new lambda 1e-7", {"pert": 1}),
+                 ("jfnk", "pert_new lambda 1e-6", {"pert": 1, "lam": 1e-6}),
+                 ("jfnk", "alpha1 1", {"alpha1": 1.0}),
+                 ("jfnk", "eta 1e-2", {"eta": 1e-2})]
+    for T_inf in T_list:
         wl = W.make_isentropic_vortex(n, T_inf)
         nc = wl.ncell
         u_exact = torch.as_tensor(W.make_isentropic_vortex(n, T_inf, x_shift=t_end).X0[2 * nc:3 * nc],
                                   device="cuda")
         mach = 0.75 / (2.0 * math.pi * math.sqrt(wl.gamma * T_inf))
-        for cfl_adv in (0.01, 0.03, 0.1, 0.3, 1.0, 3.0):
+        for cfl_adv in cfls:
             nsteps = max(1, round(t_end / (cfl_adv * dx)))
             dt = t_end / nsteps
-            for arm in ("jfnk", "si"):
-                theta = 0.5 if arm == "jfnk" else 1.0
-                o = jf.default_options(**{"theta": theta, "precond": 1, "precision": prec, **CLI_OPTS})
-                S = jf.Solver.from_workload(wl, o)
-                X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
-                err, newton, gmres = None, 0, 0
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(nsteps):
-                    try:
-                        if arm == "jfnk":
-                            st = S.step(X, dt, NEWTON_TOL, ETA)
-                            newton += st["newton_iterations"]
-                            gmres += st["gmres_iterations_total"]
-                        else:
-                            S.si_step(X, dt)
-                    except jf.JFNKError as e:
-                        err = str(e)
-                        break
-                torch.cuda.synchronize()
-                el = time.perf_counter() - t0
-                d = X[2 * nc:3 * nc] - u_exact
-                ok = err is None and bool(torch.isfinite(d).all())
-                line = {"study": "vortex", "arm": arm, "T_inf": T_inf, "mach": mach, "cfl_adv": cfl_adv,
-                        "cfl_hydro": dt * (1.0 + math.sqrt(wl.gamma * T_inf)) / dx, "steps": nsteps, "wall_s": el,
-                        "L1": float(d.abs().mean()) if ok else None,
-                        "L2": float(d.pow(2).mean().sqrt()) if ok else None,
-                        "Linf": float(d.abs().max()) if ok else None, "error": err if err else (None if ok else
-                                                                                          "non-finite state")}
-                if arm == "jfnk":
-                    line["newton_per_step"] = newton / nsteps
-                    line["gmres_per_newton"] = gmres / max(1, newton)
-                print(json.dumps(line), flush=True)
+            for arm, name, kw in cases:
+                opts = {"newton_tol": NEWTON_TOL, "eta": ETA, **CLI_OPTS, **kw}
+                r = vortex_run(jf, wl, u_exact, dt, nsteps, arm, prec, opts)
+                print(json.dumps({"study": args.study, "arm": arm, "variant": name, "T_inf": T_inf, "mach": mach,
+                                  "cfl_adv": cfl_adv, "cfl_hydro": dt * (1.0 + math.sqrt(wl.gamma * T_inf)) / dx,
+                                  "steps": nsteps, **r}), flush=True)
 
 
 def main():
@@ -536,9 +563,10 @@ def main():
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
-    ap.add_argument("--study", choices=["tgv", "vortex"], default=None,
+    ap.add_argument("--study", choices=["tgv", "vortex", "params"], default=None,
                     help="tgv: the Taylor-Green iteration and decay study of Sect. 5.1.2; vortex: the "
-                         "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1 (JSON lines)")
+                         "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1; params: the JFNK+PBP "
+                         "parameter variants of Sect. 5.1.1 on the vortex (JSON lines)")
     ap.add_argument("--machs", default="1e-1,1e-2,1e-3,1e-4,1e-5,1e-6", help="Mach numbers of --study tgv")
     ap.add_argument("--decay", action="store_true", help="--study tgv: decay run to t = 20")
     ap.add_argument("--study-n", type=int, default=64, help="cells per direction of --study tgv")
@@ -551,7 +579,7 @@ def main():
     if args.study == "tgv":
         study_tgv(args)
         return
-    if args.study == "vortex":
+    if args.study in ("vortex", "params"):
         study_vortex(args)
         return
     if args.only:
