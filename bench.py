@@ -44,19 +44,19 @@ ETA = 1e-4
 # jv_kernels_128cubed.md): flops = dadd + dmul + 2 dfma, instructions =
 # dadd + dmul + dfma, both divided by the cell count.  Division sequences are
 # counted as the DFMA/DMUL/DADD instructions they execute.
-FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 6.0, "face_fluxes": 85.0, "mom_fluxes": 120.0, "assemble": 117.9}
-FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 71.0, "mom_fluxes": 96.0, "assemble": 85.9}
+FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 6.0, "face_fluxes": 85.0, "mom_fluxes": 120.0, "assemble": 102.9}
+FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 71.0, "mom_fluxes": 96.0, "assemble": 70.9}
 # DRAM bytes per cell per launch from the same capture (dram__bytes_read +
 # dram__bytes_write); at 128^3 part of the reads hit the 129 MB L2, so these
 # are lower bounds for 256^3 (where the algorithmic bytes below apply).
-DRAM_BYTES_PER_CELL_128 = {"perturb": 128.1, "eos": 17.2, "face_fluxes": 86.3, "mom_fluxes": 98.4,
-                           "assemble": 265.5}
+DRAM_BYTES_PER_CELL_128 = {"perturb": 128.2, "eos": 17.1, "face_fluxes": 86.3, "mom_fluxes": 98.6,
+                           "assemble": 305.8}
 JV_KERNELS = ["perturb", "eos", "face_fluxes", "mom_fluxes", "assemble"]
 # Algorithmic HBM bytes per cell of one launch of each Jv kernel (3D, FP64
 # state, FP32 Krylov vectors; each array the kernel must touch read or
 # written once).
 HBM_BYTES_PER_CELL = {"perturb": 5 * (8 + 4 + 8 + 8), "eos": 2 * 8 + 2 * 8, "face_fluxes": 5 * 8 + 2 * 8 + 6 * 8,
-                      "mom_fluxes": 3 * 8 + 3 * 8 + 9 * 8, "assemble": 5 * 8 + 8 + 6 * 8 + 9 * 8 + 5 * 8 * 2 + 5 * 4}
+                      "mom_fluxes": 3 * 8 + 3 * 8 + 9 * 8, "assemble": 5 * 8 + 8 + 6 * 8 + 9 * 8 + 5 * 8 * 3 + 5 * 4}
 
 
 def load_peaks():
@@ -200,10 +200,11 @@ def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
     return S, X0, dt, ms, stats
 
 
-def e2e_arm(jf, wl, precision, steps, device, stream):
+def e2e_arm(jf, wl, precision, steps, warmup, device, stream):
     """Same metric through the public API with HOST buffers: every step copies
     the state from pinned host memory to the device, steps, and copies the
-    new state back."""
+    new state back.  The same warm-up steps as the device arm come first, so
+    both time the same steps of the run."""
     import torch
     o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision, **OPT_OVERRIDES)
     S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
@@ -212,6 +213,11 @@ def e2e_arm(jf, wl, precision, steps, device, stream):
     with torch.cuda.stream(stream):
         X.copy_(host, non_blocking=True)
     dt = S.dt_from_cfl(X, wl.cfl_hydro)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            X.copy_(host, non_blocking=True)
+            S.step(X, dt, NEWTON_TOL, ETA)
+            host.copy_(X, non_blocking=True)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -246,7 +252,7 @@ def oracle_sample(n_small=32, steps=1):
 
 
 def reference_main(args, ws, rank):
-    n_small = 32
+    n_small = args.ref_n
     if rank != 0:
         return
     for _ in range(args.warmup):
@@ -545,6 +551,62 @@ def study_vortex(args):
                                   "steps": nsteps, **r}), flush=True)
 
 
+def study_inner(args):
+    """--study inner: accuracy of the inner SI solve (the paper's eta' of
+    Sect. 3.5, here the number of V-cycles: about 0.1 residual reduction
+    each, so 1, 2, 4, 8 cycles stand for eta' ~ 1e-1, 1e-2, 1e-4, 1e-8) and
+    SI coefficients from each Newton iterate or frozen at X^n, on the
+    Taylor-Green vortex 64^3 (M = 1e-2, 1e-4, CFL_adv = 0.5, after 100 steps
+    at CFL_hydro = 1) and on problem 2 at 256^2 (conduction, CFL 100):
+    GMRES iterations per Newton iteration and step rate."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    import workloads as W
+    prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
+    cases = []
+    for mach in (1e-2, 1e-4):
+        wl = W.make_tgv(64, mach)
+        S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec))
+        X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+        dt1 = S.dt_from_cfl(X, 1.0)
+        for _ in range(100):
+            S.step(X, dt1, NEWTON_TOL, ETA)
+        dt = 0.5 * (2.0 * math.pi / 64) / tgv_speed_max(X, wl.ncell)
+        cases.append((f"tgv64 M={mach:g}", wl, X.clone(), dt))
+    wl = W.config(2)
+    X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec))
+    cases.append(("problem2 256^2", wl, X, S.dt_from_cfl(X, wl.cfl_hydro)))
+    for name, wl, X0, dt in cases:
+        for cycles in (1, 2, 4, 8):
+            for freeze in (0, 1):
+                o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, mg_cycles=cycles,
+                                       pc_freeze=freeze)
+                S = jf.Solver.from_workload(wl, o)
+                X = X0.clone()
+                nn = ng = 0
+                err = None
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                k = 0
+                for k in range(args.steps):
+                    try:
+                        st = S.step(X, dt, NEWTON_TOL, ETA)
+                    except jf.JFNKError as e:
+                        err = str(e)
+                        break
+                    nn += st["newton_iterations"]
+                    ng += st["gmres_iterations_total"]
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                print(json.dumps({"study": "inner", "case": name, "mg_cycles": cycles, "pc_freeze": freeze,
+                                  "steps": args.steps, "steps_per_s": args.steps / el if err is None else None,
+                                  "newton_per_step": nn / max(1, k + (err is None)),
+                                  "gmres_per_newton": ng / max(1, nn), "error": err}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -563,13 +625,16 @@ def main():
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
-    ap.add_argument("--study", choices=["tgv", "vortex", "params"], default=None,
+    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner"], default=None,
                     help="tgv: the Taylor-Green iteration and decay study of Sect. 5.1.2; vortex: the "
                          "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1; params: the JFNK+PBP "
-                         "parameter variants of Sect. 5.1.1 on the vortex (JSON lines)")
+                         "parameter variants of Sect. 5.1.1 on the vortex; inner: V-cycle count and frozen "
+                         "coefficients (JSON lines)")
     ap.add_argument("--machs", default="1e-1,1e-2,1e-3,1e-4,1e-5,1e-6", help="Mach numbers of --study tgv")
     ap.add_argument("--decay", action="store_true", help="--study tgv: decay run to t = 20")
     ap.add_argument("--study-n", type=int, default=64, help="cells per direction of --study tgv")
+    ap.add_argument("--ref-n", type=int, default=32,
+                    help="cells per direction of the oracle sample (--impl reference, cpu_baseline)")
     ap.add_argument("--sweep", action="store_true", help="--study tgv: GMRES iterations against CFL_hydro")
     args = ap.parse_args()
     for k in ("mg_cycles", "mg_nu1", "mg_nu2", "pc_freeze"):
@@ -581,6 +646,9 @@ def main():
         return
     if args.study in ("vortex", "params"):
         study_vortex(args)
+        return
+    if args.study == "inner":
+        study_inner(args)
         return
     if args.only:
         kernel_main(args)
@@ -660,14 +728,14 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        ms_e2e, nbytes = e2e_arm(jf, wl, jf.MIXED, args.steps, device, stream)
+        ms_e2e, nbytes = e2e_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream)
         ms_e2e = max_over_ranks(ws, ms_e2e)
         e2e = {"value": ws * args.steps / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_small = 32
+        n_small = args.ref_n
         s, threads = oracle_sample(n_small, 1)
         v = (n_small / args.n) ** 3 / s
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -40,6 +40,9 @@ struct jfnk_handle {
     // adjoint (FP64): VJP scratch, its output, transposed-preconditioner
     // temporaries, right-hand side, multiplier and a scaled input vector
     double *adj, *Xb, *rub, *reb, *rpb, *b64, *lam, *w64;
+    // coefficients of the Jacobian-free product of the current linearisation:
+    // jvP = L^-1/dt, jvQ = theta L^-1, jvC = L^-1 G(X)
+    double *jvP, *jvQ, *jvC;
     long long npartials;
     long long ldv;     // column stride of V and Z: nvec rounded up to 64 (16-byte aligned columns)
     std::vector<MGLevel> levels;
@@ -113,6 +116,9 @@ size_t plan(jfnk_handle* h, char* base) {
     h->b64 = (double*)take(nv * 8);
     h->lam = (double*)take(nv * 8);
     h->w64 = (double*)take(nv * 8);
+    h->jvP = (double*)take(nv * 8);
+    h->jvQ = (double*)take(nv * 8);
+    h->jvC = (double*)take(nv * 8);
     const size_t e = h->elt;
     h->V = take((size_t)(m + 1) * h->ldv * e);
     h->Z = take((size_t)m * h->ldv * e);
@@ -273,7 +279,7 @@ void jv(jfnk_handle* h, const double* X, double dt, const TZ* z, int znorm_ready
     if (prof) cudaEventRecord(h->ev[3], s);
     launch_mom_fluxes(h->G, h->Xp, h->Fm, h->Psi, s);
     if (prof) cudaEventRecord(h->ev[4], s);
-    launch_assemble<kModeJv, T>(h->G, h->Xp, h->p, h->Fm, h->FE, h->Psi, h->bn, h->G0, h->Linv, h->scal, kSlotDelta,
+    launch_assemble<kModeJv, T>(h->G, h->Xp, h->p, h->Fm, h->FE, h->Psi, h->jvQ, h->jvC, h->jvP, h->scal, kSlotDelta,
                                 dt, nullptr, out, s);
     if (prof) cudaEventRecord(h->ev[5], s);
 }
@@ -408,6 +414,7 @@ template <typename T>
 void linearize(jfnk_handle* h, const double* X, double dt, bool full_setup) {
     scaling(h, X);
     eval<kModeNewton, T>(h, X, dt, h->G0, Vcol<T>(h, 0));
+    launch_jv_coeffs(h->Linv, h->G0, dt, h->opt.theta, h->jvP, h->jvQ, h->jvC, h->nvec, h->stream);
     if (full_setup) {
         si_setup(h, X, dt);
     } else if (h->nf > 0) {
@@ -716,6 +723,7 @@ jfnk_status jfnk_jv(jfnk_handle* h, const double* X, double dt, const void* v, v
     if (!X || !v || !Jv || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_jv");
     scaling(h, X);
     eval<kModeG, double>(h, X, dt, h->G0, (double*)nullptr);
+    launch_jv_coeffs(h->Linv, h->G0, dt, h->opt.theta, h->jvP, h->jvQ, h->jvC, h->nvec, h->stream);
     if (h->mixed) jv<float, float>(h, X, dt, (const float*)v, 0, (float*)Jv);
     else jv<double, double>(h, X, dt, (const double*)v, 0, (double*)Jv);
     if (delta_used) {

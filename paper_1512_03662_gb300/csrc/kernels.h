@@ -21,6 +21,7 @@ enum {
     kSlotMaxSpeed = 6,   // max |u| + c_s
     kSlotTmp = 7,
     kSlotBeta0 = 8,
+    kSlotInvDelta = 9,   // 1/delta of the current Jv (one division, not one per thread)
     kNumSlots = 16
 };
 
@@ -82,6 +83,10 @@ void launch_restart_residual(T* r, const double* G0, const double* bn, const dou
                              cudaStream_t s);
 void launch_init_cycle(double* scal, double* g, double* vscale, int m, cudaStream_t s);
 void launch_add_col(double* col, const double* other, int n, cudaStream_t s);
+// coefficients of the Jacobian-free product for one linearisation:
+// P = L^-1 / dt, Q = theta L^-1, C = L^-1 G(X)
+void launch_jv_coeffs(const double* Linv, const double* G0, double dt, double theta, double* P, double* Q, double* C,
+                      long long n, cudaStream_t s);
 
 // precond.cu
 struct MGLevel {

@@ -83,13 +83,16 @@ void launch_finalize(const double* partials, int n, double* scal, int slot, int 
 
 __global__ void k_delta(double* scal, double lambda, int pert) {
     double zn = scal[kSlotZnorm];
+    double d;
     if (pert == 0) {
-        scal[kSlotDelta] = lambda * (lambda + scal[kSlotXhatNorm] / zn);
+        d = lambda * (lambda + scal[kSlotXhatNorm] / zn);
     } else {
         double uv = scal[kSlotTmp];
         double sgn = uv >= 0.0 ? 1.0 : -1.0;
-        scal[kSlotDelta] = lambda * (1e-12 / lambda + fabs(uv) / (zn * zn)) * sgn;
+        d = lambda * (1e-12 / lambda + fabs(uv) / (zn * zn)) * sgn;
     }
+    scal[kSlotDelta] = d;
+    scal[kSlotInvDelta] = 1.0 / d;
 }
 
 void launch_delta(double* scal, double lambda, int pert, cudaStream_t s) { k_delta<<<1, 1, 0, s>>>(scal, lambda, pert); }
@@ -664,6 +667,22 @@ void launch_init_cycle(double* scal, double* g, double* vscale, int m, cudaStrea
 __global__ void k_add_col(double* col, const double* other, int n) {
     int i = threadIdx.x;
     if (i < n) col[i] += other[i];
+}
+
+__global__ void k_jv_coeffs(const double* __restrict__ Linv, const double* __restrict__ G0, double idt, double theta,
+                            double* __restrict__ P, double* __restrict__ Q, double* __restrict__ C, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double li = Linv[e];
+        P[e] = idt * li;
+        Q[e] = theta * li;
+        C[e] = G0[e] * li;
+    }
+}
+
+void launch_jv_coeffs(const double* Linv, const double* G0, double dt, double theta, double* P, double* Q, double* C,
+                      long long n, cudaStream_t s) {
+    ++g_launch_count;
+    k_jv_coeffs<<<kRedBlocks, kBlock, 0, s>>>(Linv, G0, 1.0 / dt, theta, P, Q, C, n);
 }
 
 void launch_add_col(double* col, const double* other, int n, cudaStream_t s) {

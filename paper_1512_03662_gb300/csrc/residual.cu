@@ -212,7 +212,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
     constexpr int nd = ND;
     const double th = G.theta;
     double inv_delta = 0.0;
-    if (MODE == kModeJv) inv_delta = 1.0 / scal[delta_slot];
+    if (MODE == kModeJv) inv_delta = scal[kSlotInvDelta];
 
     double Rr = 0.0, RE = 0.0, divu = 0.0;
 #pragma unroll
@@ -282,9 +282,12 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
             double g = Uv[k] * dt_inv - th * Rv[k];
             outd[j] = g;
             outb[j] = wall ? (TO)0 : (TO)(-((g - bn[j]) * Linv[j]));
-        } else {  // kModeJv
-            double g = Uv[k] * dt_inv - th * Rv[k];
-            outb[j] = wall ? (TO)0 : (TO)((g - G0[j]) * inv_delta * Linv[j]);
+        } else {
+            // kModeJv: L^-1 (G(X+dw) - G(X)) / delta with bn, G0, Linv holding
+            // Q = theta L^-1, C = L^-1 G(X) and P = L^-1/dt (launch_jv_coeffs):
+            // (U P - R Q - C) / delta, two FMAs and a product per unknown
+            const double q = fma(Rv[k], bn[j], G0[j]);
+            outb[j] = wall ? (TO)0 : (TO)(fma(Uv[k], Linv[j], -q) * inv_delta);
         }
     }
 }
