@@ -197,7 +197,7 @@ def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     S.set_profiling(False)
-    return S, X0, dt, ms, stats
+    return S, X0, dt, ms, stats, X
 
 
 def e2e_arm(jf, wl, precision, steps, warmup, device, stream):
@@ -278,8 +278,9 @@ def reference_main(args, ws, rank):
 
 
 def kernel_main(args):
-    """--only jv|precond: repeated Jacobian-free products (or preconditioner
-    applies) at one state of the workload, for kernel profiling."""
+    """--only jv|precond|vjp: repeated Jacobian-free products, preconditioner
+    applies or transposed residual Jacobian products (vjp, FP64) at one state
+    of the workload, for kernel timing and profiling."""
     import torch
     from paper_1512_03662_gb300 import build as B
     B.build()
@@ -288,7 +289,7 @@ def kernel_main(args):
     device = torch.device("cuda:0")
     stream = torch.cuda.Stream(device)
     wl = make_workload(args.n)
-    prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
+    prec = jf.FP64 if (args.precision == "fp64" or args.only == "vjp") else jf.MIXED
     # a single Jv or preconditioner call needs no Krylov basis: restart length 1
     o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, gmres_m=1, **OPT_OVERRIDES)
     S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
@@ -296,7 +297,12 @@ def kernel_main(args):
     dt = S.dt_from_cfl(X, wl.cfl_hydro)
     v = torch.as_tensor(W.random_vector(wl, 3), device=device).to(S.vdtype)
     out = torch.empty_like(v)
-    call = (lambda: S.jv(X, dt, v, out)) if args.only == "jv" else (lambda: S.precond_apply(X, dt, v, out))
+    if args.only == "jv":
+        call = lambda: S.jv(X, dt, v, out)                  # noqa: E731
+    elif args.only == "precond":
+        call = lambda: S.precond_apply(X, dt, v, out)       # noqa: E731
+    else:
+        call = lambda: S.vjp_residual(X, dt, v)             # noqa: E731
     for _ in range(args.warmup):
         call()
     torch.cuda.synchronize()
@@ -308,7 +314,8 @@ def kernel_main(args):
         e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"only": args.only, "n": args.n, "precision": args.precision, "ms_per_call": ms,
+    print(json.dumps({"only": args.only, "n": args.n, "precision": "fp64" if prec == jf.FP64 else "mixed",
+                      "ms_per_call": ms,
                       "gcell_s": wl.ncell / (ms / 1e3) / 1e9}))
 
 
@@ -607,6 +614,70 @@ def study_inner(args):
                                   "gmres_per_newton": ng / max(1, nn), "error": err}), flush=True)
 
 
+def study_adjoint(args):
+    """--study adjoint: the gradient of the adjoint workload (problem 5,
+    128^2, 4 implicit steps at CFL_hydro = 50, FP64): loss = final kinetic
+    energy, gradients with respect to the initial temperature perturbation
+    field and K0 by one transposed Newton-system solve per step (jfnk_vjp),
+    as torch.autograd does through JFNKStep.  Times the forward steps and
+    the backward pass and reports the GMRES iterations of both."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    import workloads as W
+    wl = W.config(5)
+    nc = wl.ncell
+    o = jf.default_options(**{"theta": wl.theta, "precond": wl.precond, "precision": jf.FP64, "eta": 1e-10,
+                              **CLI_OPTS})
+    S = jf.Solver.from_workload(wl, o)
+    X0 = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+    dt = S.dt_from_cfl(X0, wl.cfl_hydro)
+    n = round(math.sqrt(nc))
+
+    dV = wl.dx[0] * wl.dx[1]
+
+    def kinetic_energy_grad(X):
+        """d/dX of the sum over faces of rho_f u_f^2 / 2 dV (periodic in x,
+        walls in y: the y slot 0 is the wall face, zero, and jfnk_vjp masks
+        wall slots of the gradient it receives)"""
+        Xg = X.detach().clone().requires_grad_(True)
+        rho = Xg[:nc].reshape(n, n)
+        ke = 0.0
+        for c in range(2):
+            u = Xg[(2 + c) * nc:(3 + c) * nc].reshape(n, n)
+            rl = torch.roll(rho, 1, dims=1 - c)
+            ke = ke + (0.25 * (rl + rho) * u * u).sum() * dV
+        ke.backward()
+        return Xg.grad.detach()
+
+    for rep in range(2):                                   # the first repetition warms up
+        traj = [X0.clone()]
+        fstats = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(wl.n_steps):
+            X = traj[-1].clone()
+            fstats.append(S.step(X, dt, 1e-12, 1e-10))
+            traj.append(X)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        g = kinetic_energy_grad(traj[-1])
+        gk, bits = 0.0, []
+        for k in range(wl.n_steps, 0, -1):
+            gXn, gK0, st, code = S.vjp(traj[k - 1], traj[k], dt, g)
+            g, gk = gXn, gk + gK0
+            bits.append(st["gmres_iterations_total"])
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    line = {"study": "adjoint", "workload": "adjoint2d 128^2 (problem 5), 4 steps, CFL_hydro 50, FP64",
+            "forward_ms": 1e3 * (t1 - t0), "backward_ms": 1e3 * (t2 - t1), "backward_over_forward": (t2 - t1) / (t1 - t0),
+            "forward_newton": [s["newton_iterations"] for s in fstats],
+            "forward_gmres": [s["gmres_iterations_total"] for s in fstats],
+            "adjoint_gmres": bits[::-1], "grad_norm": float(g.norm()), "dL_dK0": gk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,7 +688,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", choices=["jv", "precond"], default=None,
+    ap.add_argument("--only", choices=["jv", "precond", "vjp"], default=None,
                     help="time only repeated Jv or preconditioner calls (profiling)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--mg-cycles", type=int, default=None, help="multigrid V-cycles per preconditioner apply")
@@ -625,11 +696,12 @@ def main():
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
-    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner"], default=None,
+    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner", "adjoint"], default=None,
                     help="tgv: the Taylor-Green iteration and decay study of Sect. 5.1.2; vortex: the "
                          "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1; params: the JFNK+PBP "
                          "parameter variants of Sect. 5.1.1 on the vortex; inner: V-cycle count and frozen "
-                         "coefficients (JSON lines)")
+                         "coefficients; adjoint: forward and backward time of the adjoint workload "
+                         "(JSON lines)")
     ap.add_argument("--machs", default="1e-1,1e-2,1e-3,1e-4,1e-5,1e-6", help="Mach numbers of --study tgv")
     ap.add_argument("--decay", action="store_true", help="--study tgv: decay run to t = 20")
     ap.add_argument("--study-n", type=int, default=64, help="cells per direction of --study tgv")
@@ -649,6 +721,9 @@ def main():
         return
     if args.study == "inner":
         study_inner(args)
+        return
+    if args.study == "adjoint":
+        study_adjoint(args)
         return
     if args.only:
         kernel_main(args)
@@ -675,7 +750,7 @@ def main():
     clocks = ClockSampler(local)
     barrier(ws)
     clocks.start()
-    S, X0, dt, ms_mixed, st_mixed = run_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream, True)
+    S, X0, dt, ms_mixed, st_mixed, X_mixed = run_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream, True)
     so = S.options
     solver_cfg = {"newton_tol": NEWTON_TOL, "eta": ETA, "gmres_m": so.gmres_m, "precond": so.precond,
                   "mg_cycles": so.mg_cycles, "mg_nu1": so.mg_nu1, "mg_nu2": so.mg_nu2, "pc_freeze": so.pc_freeze}
@@ -685,13 +760,30 @@ def main():
 
     fp64 = None
     if not args.no_fp64:
-        S64, _, _, ms64, st64 = run_arm(jf, wl, jf.FP64, args.steps, args.warmup, device, stream, True)
+        S64, _, _, ms64, st64, X64 = run_arm(jf, wl, jf.FP64, args.steps, args.warmup, device, stream, True)
+        # the same steps in both precisions: max over unknowns of |X_mixed - X_fp64| / R(X_fp64)
+        _, R64, _ = S64.scaling(X64)
+        mixed_vs_fp64 = float(((X_mixed - X64) / R64).abs().max())
+        # residual evaluations (F of X^{n+1} against X^n, FP64) per second
+        F = torch.empty_like(X64)
+        S64.residual(X64, X0, dt, F)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            r0.record(stream)
+            for _ in range(5):
+                S64.residual(X64, X0, dt, F)
+            r1.record(stream)
+        torch.cuda.synchronize()
+        residual_gcell_s = 5 * wl.ncell / (r0.elapsed_time(r1) / 1e3) / 1e9
+        del F, X64, R64
         ms64 = max_over_ranks(ws, ms64)
         fp64 = {"steps_per_s": ws * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
                 "newton_per_step": sum(s["newton_iterations"] for s in st64) / len(st64),
                 "gmres_per_newton": sum(s["gmres_iterations_total"] for s in st64) /
                 max(1, sum(s["newton_iterations"] for s in st64)),
-                "jv_gcell_s": None}
+                "jv_gcell_s": None, "residual_gcell_s": residual_gcell_s,
+                "mixed_vs_fp64_max_scaled_diff": mixed_vs_fp64}
         jv64 = sum(s["jv_ms"] for s in st64)
         njv64 = sum(s["jv_evaluations"] for s in st64)
         if jv64 > 0:

@@ -69,30 +69,39 @@ struct UpwindD {
     double v, dn, df, dot;
 };
 
-__device__ __forceinline__ UpwindD upwind_d(double q_near, double q_far, double q_other) {
+// value and derivatives from the differences and inv = 1/(a+b) (any value
+// where the limiter is off): with s = a + b, h_a = (b/s)^2, h_b = (a/s)^2
+__device__ __forceinline__ UpwindD upwind_d_finish(double q_near, double a, double b, bool on, double inv) {
+    const double ai = a * inv, bi = b * inv;
+    const double ha = on ? bi * bi : 0.0, hb = on ? ai * ai : 0.0;
     UpwindD r;
-    double a = q_near - q_far;
-    double b = q_other - q_near;
-    double ab = a * b;
-    if (ab > 0.0) {
-        double s = a + b;
-        double ha = (b * b) / (s * s), hb = (a * a) / (s * s);
-        r.v = q_near + ab / s;
-        r.dn = 1.0 + ha - hb;
-        r.df = -ha;
-        r.dot = hb;
-    } else {
-        r.v = q_near;
-        r.dn = 1.0;
-        r.df = 0.0;
-        r.dot = 0.0;
-    }
+    r.v = q_near + (on ? (a * b) * inv : 0.0);
+    r.dn = 1.0 + ha - hb;
+    r.df = -ha;
+    r.dot = hb;
     return r;
 }
 
-__device__ __forceinline__ double cond_chi(const Grid& G, double T) {
-    return G.chi3 ? G.K0 * (T * T * T) : G.K0 * pow(T, G.chi_exp);
+// branch-free, one reciprocal
+__device__ __forceinline__ UpwindD upwind_d(double q_near, double q_far, double q_other) {
+    const double a = q_near - q_far;
+    const double b = q_other - q_near;
+    const bool on = positive(a * b);
+    return upwind_d_finish(q_near, a, b, on, 1.0 / (on ? a + b : 1.0));
 }
+
+// two face values with one division (batched inversion)
+__device__ __forceinline__ void upwind_d2(double qn1, double qf1, double qo1, double qn2, double qf2, double qo2,
+                                          UpwindD& r1, UpwindD& r2) {
+    const double a1 = qn1 - qf1, b1 = qo1 - qn1, a2 = qn2 - qf2, b2 = qo2 - qn2;
+    const bool on1 = positive(a1 * b1), on2 = positive(a2 * b2);
+    const double den[2] = {on1 ? a1 + b1 : 1.0, on2 ? a2 + b2 : 1.0};
+    double inv[2];
+    recip_all<2>(den, inv);
+    r1 = upwind_d_finish(qn1, a1, b1, on1, inv[0]);
+    r2 = upwind_d_finish(qn2, a2, b2, on2, inv[1]);
+}
+
 __device__ __forceinline__ double cond_dchi(const Grid& G, double T) {
     return G.chi3 ? 3.0 * G.K0 * (T * T) : G.K0 * G.chi_exp * pow(T, G.chi_exp - 1.0);
 }
@@ -210,7 +219,7 @@ __global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __
                 m = Fmh[c * nc + cc] + (hasup ? Fmh[c * nc + ju] : 0.0);
                 jm1 = c * nc + cc;
                 jm2 = hasup ? c * nc + ju : -1;
-                const bool left = m >= 0.0;
+                const bool left = nonneg(m);
                 on[c] = left ? 0 : 1;
                 of[c] = left ? -1 : 2;
                 oo[c] = left ? 1 : 0;
@@ -221,7 +230,7 @@ __global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __
                 m = Fmh[d * nc + jl] + Fmh[d * nc + cc];
                 jm1 = d * nc + jl;
                 jm2 = d * nc + cc;
-                const bool left = m >= 0.0;
+                const bool left = nonneg(m);
                 on[d] = left ? -1 : 0;
                 of[d] = left ? -2 : 1;
                 oo[d] = left ? 0 : -1;
@@ -248,7 +257,7 @@ __global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __
 // --------------------------------------------------------------------------
 template <int ND>
 __global__ void k_vjp_face(Grid G, const double* __restrict__ X, const double* __restrict__ p,
-                           const double* __restrict__ T, AdjBufs A) {
+                           const double* __restrict__ T, const double* __restrict__ chi, AdjBufs A) {
     Idx3 P;
     long long c;
     if (!cell_pos(G.n, P, c)) return;
@@ -262,7 +271,7 @@ __global__ void k_vjp_face(Grid G, const double* __restrict__ X, const double* _
         if (fmhb == 0.0 && feb == 0.0) continue;
         const bool wall = is_wall_slot(G, d, P);
         const double u = load_normal(G, X + (2 + d) * nc, d, P, 0, 0, 0);
-        const bool left = u >= 0.0;
+        const bool left = nonneg(u);
         int on[3] = {0, 0, 0}, of[3] = {0, 0, 0}, oo[3] = {0, 0, 0};
         on[d] = left ? -1 : 0;
         of[d] = left ? -2 : 1;
@@ -270,8 +279,8 @@ __global__ void k_vjp_face(Grid G, const double* __restrict__ X, const double* _
         const long long jn = cell_slot(G, P, on[0], on[1], on[2]);
         const long long jf = cell_slot(G, P, of[0], of[1], of[2]);
         const long long jo = cell_slot(G, P, oo[0], oo[1], oo[2]);
-        const UpwindD Ur = upwind_d(rho[jn], rho[jf], rho[jo]);
-        const UpwindD Ue = upwind_d(E[jn], E[jf], E[jo]);
+        UpwindD Ur, Ue;
+        upwind_d2(rho[jn], rho[jf], rho[jo], E[jn], E[jf], E[jo], Ur, Ue);
         const double fm = u * Ur.v;
         const double fmb = 0.5 * fmhb + feb * Ue.v;
         const double Eupb = feb * fm;
@@ -298,7 +307,7 @@ __global__ void k_vjp_face(Grid G, const double* __restrict__ X, const double* _
             // FE contains -q, q = (chi_L + chi_R)/2 (T_R - T_L) / dx
             const double qb = -feb;
             const double Tl = T[jl], Tc = T[c];
-            const double chif = 0.5 * (cond_chi(G, Tl) + cond_chi(G, Tc));
+            const double chif = 0.5 * (chi[jl] + chi[c]);      // chi of the forward k_eos
             const double dT = (Tc - Tl) * G.idx[d];
             atomicAdd(A.chib + jl, 0.5 * qb * dT);
             atomicAdd(A.chib + c, 0.5 * qb * dT);
@@ -384,8 +393,8 @@ __global__ void k_dRdK0_dot(Grid G, const double* __restrict__ T, const double* 
         else KERNEL<2><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);                       \
     } while (0)
 
-void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* Fmh, const double* w,
-                double a_u, double b_r, double* adj, double* Xb, cudaStream_t s) {
+void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* chi, const double* Fmh,
+                const double* w, double a_u, double b_r, double* adj, double* Xb, cudaStream_t s) {
     const long long nc = G.ncell, nd = G.ndim;
     AdjBufs A;
     A.Fmhb = adj;
@@ -400,7 +409,7 @@ void launch_vjp(const Grid& G, const double* X, const double* p, const double* T
     launch_zero<double>(Xb, (2 + nd) * nc, s);
     CELL_LAUNCH_A(k_vjp_assemble, G, X, p, w, a_u, b_r, A);
     CELL_LAUNCH_A(k_vjp_mom, G, X, Fmh, A);
-    CELL_LAUNCH_A(k_vjp_face, G, X, p, T, A);
+    CELL_LAUNCH_A(k_vjp_face, G, X, p, T, chi, A);
     CELL_LAUNCH_A(k_vjp_eos, G, X, T, A);
 }
 

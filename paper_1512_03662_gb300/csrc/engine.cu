@@ -449,7 +449,7 @@ void vjp_apply(jfnk_handle* h, const double* Xs, const double* w, double a, doub
     cudaStream_t s = h->stream;
     launch_eos(h->G, Xs, h->p, h->T, h->chi, s);
     launch_face_fluxes(h->G, Xs, h->p, h->T, h->chi, h->Fm, h->FE, s);
-    launch_vjp(h->G, Xs, h->p, h->T, h->Fm, w, a, b, h->adj, out, s);
+    launch_vjp(h->G, Xs, h->p, h->T, h->chi, h->Fm, w, a, b, h->adj, out, s);
 }
 
 // z = M^-T y (transpose of the scaled physics-based preconditioner)

@@ -143,10 +143,10 @@ void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* r
                         const MGLevel& L0, T* z, double* partials, cudaStream_t s);
 
 // adjoint.cu
-// y = (a dU/dX + b dR/dX)^T w at X (p, T, half mass fluxes of X precomputed);
+// y = (a dU/dX + b dR/dX)^T w at X (p, T, chi and half mass fluxes of X precomputed);
 // adj: vjp_scratch_doubles(G) doubles of scratch
-void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* Fmh, const double* w,
-                double a_u, double b_r, double* adj, double* Xb, cudaStream_t s);
+void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* chi, const double* Fmh,
+                const double* w, double a_u, double b_r, double* adj, double* Xb, cudaStream_t s);
 long long vjp_scratch_doubles(const Grid& G);
 // partial sums of w_E . (conduction divergence / K0) (T of the state given)
 void launch_dRdK0_dot(const Grid& G, const double* T, const double* w, double* partials, cudaStream_t s);
