@@ -55,7 +55,7 @@ JV_KERNELS = ["perturb", "eos", "face_fluxes", "mom_fluxes", "assemble"]
 # Algorithmic HBM bytes per cell of one launch of each Jv kernel (3D, FP64
 # state, FP32 Krylov vectors; each array the kernel must touch read or
 # written once).
-HBM_BYTES_PER_CELL = {"perturb": 5 * (8 + 4 + 8 + 8), "eos": 2 * 8 + 2 * 8, "face_fluxes": 5 * 8 + 2 * 8 + 6 * 8,
+HBM_BYTES_PER_CELL = {"perturb": 5 * (8 + 4 + 8 + 8), "eos": 2 * 8 + 3 * 8, "face_fluxes": 5 * 8 + 3 * 8 + 6 * 8,
                       "mom_fluxes": 3 * 8 + 3 * 8 + 9 * 8, "assemble": 5 * 8 + 8 + 6 * 8 + 9 * 8 + 5 * 8 * 3 + 5 * 4}
 
 
@@ -371,9 +371,9 @@ def study_tgv(args):
     import paper_1512_03662_gb300 as jf
     import workloads as W
     prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
-    n = args.study_n
+    n = args.study_n or 64
     h = 2.0 * math.pi / n
-    machs = [float(m) for m in args.machs.split(",")]
+    machs = [float(m) for m in (args.machs or "1e-1,1e-2,1e-3,1e-4,1e-5,1e-6").split(",")]
 
     def solver(wl, **kw):
         o = jf.default_options(**{"theta": wl.theta, "precond": wl.precond, "precision": prec, **CLI_OPTS, **kw})
@@ -678,6 +678,80 @@ def study_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def study_machsweep(args):
+    """--study machsweep: the 3D vortex tube (problem 3: Gresho profile in
+    x-y, uniform along z, periodic, seeded 1e-6 density noise, Crank-Nicolson,
+    CFL_hydro = 1000, sound-wave preconditioner) at --study-n^3 (default 128)
+    for each Mach number of --machs (default 1e-2, 1e-4, 1e-6): the
+    workload's five steps with the FP64 handle and with the mixed handle from
+    the same X^0.  Reports steps/s, Newton and GMRES iterations, and after
+    each step the difference of the two states: scaled (max |dX| / R), in
+    the velocity relative to max |u|, and in the pressure relative to the
+    range of the pressure fluctuation (about M^2 p).  --cfl overrides
+    CFL_hydro (at Mach 1e-2 the workload's 1000 is an advective CFL of 10,
+    where GMRES stops at its iteration cap).  The same measures against the
+    oracle, on a small grid, are a parity test."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    import workloads as W
+    n = args.study_n or 128
+    machs = [float(m) for m in (args.machs or "1e-2,1e-4,1e-6").split(",")]
+
+    def measures(wl, Xa, Xb, Rb):
+        """differences of state Xa from the reference state Xb"""
+        nc = wl.ncell
+        d = (Xa - Xb)
+        g1 = wl.gamma - 1.0
+        pa = g1 * Xa[:nc] * Xa[nc:2 * nc]
+        pb = g1 * Xb[:nc] * Xb[nc:2 * nc]
+        ub = Xb[2 * nc:]
+        return {"scaled": float((d / Rb).abs().max()),
+                "velocity": float(d[2 * nc:].abs().max() / ub.abs().max()),
+                "pressure": float((pa - pb).abs().max() / (pb.max() - pb.min()))}
+
+    def run(wl, prec, steps, X0, dt):
+        o = jf.default_options(**{"theta": wl.theta, "precond": wl.precond, "precision": prec, **CLI_OPTS})
+        S = jf.Solver.from_workload(wl, o)
+        if dt is None:
+            dt = S.dt_from_cfl(X0, wl.cfl_hydro)
+        X = X0.clone()
+        traj, stats = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            stats.append(S.step(X, dt, NEWTON_TOL, ETA))
+            traj.append(X.clone())
+        torch.cuda.synchronize()
+        return S, traj, stats, time.perf_counter() - t0, dt
+
+    for mach in machs:
+        wl = W.config(3, n=(n, n, n), mach=mach)
+        if args.cfl is not None:
+            wl.cfl_hydro = args.cfl
+        X0 = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+        line = {"study": "machsweep", "workload": f"vortextube3d {n}^3 (problem 3), CFL_hydro {wl.cfl_hydro:g}",
+                "mach": mach, "cfl_adv_approx": mach * wl.cfl_hydro, "steps": wl.n_steps}
+        arms, dt = {}, None
+        for name, prec in (("fp64", jf.FP64), ("mixed", jf.MIXED)):
+            S, traj, stats, sec, dt = run(wl, prec, wl.n_steps, X0, dt)
+            nn = sum(s["newton_iterations"] for s in stats)
+            line[name] = {"steps_per_s": wl.n_steps / sec, "newton_per_step": nn / len(stats),
+                          "gmres_per_newton": sum(s["gmres_iterations_total"] for s in stats) / max(1, nn),
+                          "steps_converged": sum(1 for s in stats if s["converged"])}
+            arms[name] = (S, traj)
+        S64, t64 = arms["fp64"]
+        diffs = []
+        for k in range(wl.n_steps):
+            _, R, _ = S64.scaling(t64[k])
+            diffs.append(measures(wl, arms["mixed"][1][k], t64[k], R))
+        line["mixed_vs_fp64_per_step"] = diffs
+        del arms, S64, t64
+        torch.cuda.empty_cache()
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,15 +770,18 @@ def main():
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
-    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner", "adjoint"], default=None,
+    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner", "adjoint", "machsweep"], default=None,
                     help="tgv: the Taylor-Green iteration and decay study of Sect. 5.1.2; vortex: the "
                          "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1; params: the JFNK+PBP "
                          "parameter variants of Sect. 5.1.1 on the vortex; inner: V-cycle count and frozen "
-                         "coefficients; adjoint: forward and backward time of the adjoint workload "
-                         "(JSON lines)")
-    ap.add_argument("--machs", default="1e-1,1e-2,1e-3,1e-4,1e-5,1e-6", help="Mach numbers of --study tgv")
+                         "coefficients; adjoint: forward and backward time of the adjoint workload; "
+                         "machsweep: FP64 and mixed steps of the 3D vortex tube per Mach number (JSON lines)")
+    ap.add_argument("--machs", default=None,
+                    help="Mach numbers of --study tgv (default 1e-1,...,1e-6) or machsweep (1e-2,1e-4,1e-6)")
     ap.add_argument("--decay", action="store_true", help="--study tgv: decay run to t = 20")
-    ap.add_argument("--study-n", type=int, default=64, help="cells per direction of --study tgv")
+    ap.add_argument("--study-n", type=int, default=None,
+                    help="cells per direction of --study tgv (default 64) or machsweep (128)")
+    ap.add_argument("--cfl", type=float, default=None, help="--study machsweep: CFL_hydro instead of 1000")
     ap.add_argument("--ref-n", type=int, default=32,
                     help="cells per direction of the oracle sample (--impl reference, cpu_baseline)")
     ap.add_argument("--sweep", action="store_true", help="--study tgv: GMRES iterations against CFL_hydro")
@@ -724,6 +801,9 @@ def main():
         return
     if args.study == "adjoint":
         study_adjoint(args)
+        return
+    if args.study == "machsweep":
+        study_machsweep(args)
         return
     if args.only:
         kernel_main(args)
@@ -764,7 +844,8 @@ def main():
         # the same steps in both precisions: max over unknowns of |X_mixed - X_fp64| / R(X_fp64)
         _, R64, _ = S64.scaling(X64)
         mixed_vs_fp64 = float(((X_mixed - X64) / R64).abs().max())
-        # residual evaluations (F of X^{n+1} against X^n, FP64) per second
+        # F(X^{n+1}; X^n) through jfnk_residual per second (each call forms b^n
+        # from X^n and G(X^{n+1}): two evaluations of R_U)
         F = torch.empty_like(X64)
         S64.residual(X64, X0, dt, F)
         torch.cuda.synchronize()
