@@ -46,6 +46,7 @@ struct jfnk_handle {
     long long npartials;
     long long ldv;     // column stride of V and Z: nvec rounded up to 64 (16-byte aligned columns)
     std::vector<MGLevel> levels;
+    size_t tail_level; // first level of the single-block V-cycle tail (levels.size(): none)
     size_t elt;        // bytes per basis element
 };
 
@@ -140,6 +141,7 @@ size_t plan(jfnk_handle* h, char* base) {
 
 void build_levels(jfnk_handle* h) {
     h->levels.clear();
+    h->tail_level = (size_t)-1;
     if (h->nf == 0) return;
     MGLevel L;
     for (int d = 0; d < 3; ++d) {
@@ -163,6 +165,15 @@ void build_levels(jfnk_handle* h) {
         C.ncell = (long long)C.n[0] * C.n[1] * C.n[2];
         h->levels.push_back(C);
     }
+    // the coarse levels (which start from zero) at or below kTailCells run
+    // as one single-block kernel when that covers at least two levels
+    const size_t nl = h->levels.size();
+    h->tail_level = nl;
+    for (size_t l = 1; l + 1 < nl; ++l)
+        if (h->levels[l].ncell <= kTailCells && nl - l <= (size_t)kTailMaxLevels) {
+            h->tail_level = l;
+            break;
+        }
 }
 
 jfnk_status check_bound(jfnk_handle* h) {
@@ -221,6 +232,10 @@ void vcycle(jfnk_handle* h, size_t l, int tr = 0, bool first = false) {
     auto& Lv = h->levels;
     if (l + 1 == Lv.size()) {
         launch_coarsest<T>(h->nf, Lv[l], s, tr);
+        return;
+    }
+    if (l == h->tail_level) {
+        launch_vcycle_tail<T>(h->G, h->nf, &Lv[l], (int)(Lv.size() - l), h->opt.mg_nu1, h->opt.mg_nu2, s, tr);
         return;
     }
     for (int k = 0; k < h->opt.mg_nu1; ++k) {

@@ -138,6 +138,14 @@ template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
 template <typename T>
 void launch_coarsest(int nf, MGLevel& C, cudaStream_t s, int tr = 0);
+// the levels levels[0 .. nlev-1] (the last one the single-cell level) of a
+// V-cycle in one single-block kernel; levels[0] starts from zero
+constexpr long long kTailCells = 4096;
+constexpr int kTailMaxLevels = 16;
+constexpr int kTailThreads = 512;
+template <typename T>
+void launch_vcycle_tail(const Grid& G, int nf, const MGLevel* levels, int nlev, int nu1, int nu2, cudaStream_t s,
+                        int tr);
 template <typename T>
 void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
                         const MGLevel& L0, T* z, double* partials, cudaStream_t s);

@@ -461,14 +461,8 @@ __device__ __forceinline__ void nb_index(const LvlDev& L, int d, int a, int b, i
 // read).  A run-time flag in its place cost the kernel 12 registers and a
 // quarter of its occupancy.
 template <typename T, int NF, int ND, bool ZS>
-__global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
-                         const T* __restrict__ rhs, int colour, int compact, int tr) {
-    const int b = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int a = compact ? 2 * t + ((b + c + colour) & 1) : t;
-    if (a >= Lv.n[0] || b >= Lv.n[1]) return;
-    if (((a + b + c) & 1) != colour) return;
+__device__ __forceinline__ void smooth_cell(const LvlDev& Lv, const T* M, const T* K, T* x, const T* rhs, int a,
+                                            int b, int c, int tr) {
     const long long cc = lflat(Lv, a, b, c);
     T dg[NF], of[NF];
 #pragma unroll
@@ -501,6 +495,18 @@ __global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict
         x[cc] = (a22 * b1 - a12 * b2) / det;
         x[Lv.nc + cc] = (a11 * b2 - a21 * b1) / det;
     }
+}
+
+template <typename T, int NF, int ND, bool ZS>
+__global__ void k_smooth(LvlDev Lv, const T* __restrict__ M, const T* __restrict__ K, T* x,
+                         const T* __restrict__ rhs, int colour, int compact, int tr) {
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    const int c = blockIdx.z;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = compact ? 2 * t + ((b + c + colour) & 1) : t;
+    if (a >= Lv.n[0] || b >= Lv.n[1]) return;
+    if (((a + b + c) & 1) != colour) return;
+    smooth_cell<T, NF, ND, ZS>(Lv, M, K, x, rhs, a, b, c, tr);
 }
 
 #define MG_DISPATCH(KERNEL, GRID, BLOCK, ...)                                                 \
@@ -557,6 +563,15 @@ __device__ __forceinline__ T fine_residual(const LvlDev& F, const T* M, const T*
     return rhs[(long long)f * F.nc + cc] - out;
 }
 
+template <typename T, int NF, int ND>
+__device__ __forceinline__ void residual_cell(const LvlDev& F, const T* M, const T* K, const T* x, const T* rhs,
+                                              T* r, int a, int b, int c, int tr) {
+    const long long cc = lflat(F, a, b, c);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        r[(long long)f * F.nc + cc] = fine_residual<T, NF, ND>(F, M, K, x, rhs, f, a, b, c, tr);
+}
+
 // fine residual r = rhs - A x: one thread per fine cell, or (red_only) per
 // colour-0 cell with the compact mapping of the smoother
 template <typename T, int NF, int ND>
@@ -568,21 +583,15 @@ __global__ void k_residual_mg(LvlDev F, const T* __restrict__ M, const T* __rest
     const int a = compact ? 2 * t + ((b + c) & 1) : t;
     if (a >= F.n[0] || b >= F.n[1]) return;
     if (red_only && ((a + b + c) & 1)) return;
-    const long long cc = lflat(F, a, b, c);
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-        r[(long long)f * F.nc + cc] = fine_residual<T, NF, ND>(F, M, K, x, rhs, f, a, b, c, tr);
+    residual_cell<T, NF, ND>(F, M, K, x, rhs, r, a, b, c, tr);
 }
 
 // coarse right-hand side = mean of the children's residuals (pairs along x,
 // then y, then z; colour-1 children count as zero when red_only); the coarse
 // correction starts from zero
 template <typename T, int NF, int ND>
-__global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __restrict__ rhsc, T* __restrict__ xc,
-                           int red_only, int zero_xc) {
-    int ic[3];
-    long long cc;
-    if (!lvl_pos(C, ic, cc)) return;
+__device__ __forceinline__ void restrict_cell(const LvlDev& F, const LvlDev& C, const T* r, T* rhsc, T* xc,
+                                              const int ic[3], long long cc, int red_only, int zero_xc) {
     const bool cx = F.n[0] != C.n[0], cy = F.n[1] != C.n[1], cz = F.n[2] != C.n[2];
     const int x0 = cx ? 2 * ic[0] : ic[0], y0 = cy ? 2 * ic[1] : ic[1], z0 = cz ? 2 * ic[2] : ic[2];
 #pragma unroll
@@ -605,6 +614,15 @@ __global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __res
     }
 }
 
+template <typename T, int NF, int ND>
+__global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __restrict__ rhsc, T* __restrict__ xc,
+                           int red_only, int zero_xc) {
+    int ic[3];
+    long long cc;
+    if (!lvl_pos(C, ic, cc)) return;
+    restrict_cell<T, NF, ND>(F, C, r, rhsc, xc, ic, cc, red_only, zero_xc);
+}
+
 template <typename T>
 void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr, int red_only) {
     const int compact = (red_only && F.n[0] % 2 == 0) ? 1 : 0;
@@ -621,18 +639,15 @@ void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t
 template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 
-// Cell-centred linear prolongation x_f += P x_c, one thread per coarse cell:
-// the thread loads the coarse neighbourhood once (3 values along each
-// coarsened direction) and updates its 2^k children.  A child at offset
+// Cell-centred linear prolongation x_f += P x_c for one coarse cell: load
+// the coarse neighbourhood once (3 values along each coarsened direction)
+// and update the cell's 2^k children.  A child at offset
 // delta along a coarsened direction interpolates 3/4 of its parent and 1/4
 // of the parent's neighbour on its side (periodic wrap; at a wall the parent
 // itself), along x, then y, then z.
 template <typename T, int NF, int ND>
-__global__ void k_prolong(int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
-                          T* __restrict__ xf) {
-    int ic[3];
-    long long cc;
-    if (!lvl_pos(C, ic, cc)) return;
+__device__ __forceinline__ void prolong_cell(int bc0, int bc1, int bc2, const LvlDev& F, const LvlDev& C,
+                                             const T* xc, T* xf, const int ic[3]) {
     const bool cd[3] = {F.n[0] != C.n[0], F.n[1] != C.n[1], F.n[2] != C.n[2]};
     const int bc[3] = {bc0, bc1, bc2};
     // coarse indices at offsets -1, 0, +1 along each direction
@@ -695,17 +710,36 @@ __global__ void k_prolong(int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T
     }
 }
 
+// one thread per coarse cell and field (blockIdx.z runs over field, then
+// coarse z): one field's 27 coarse values live at a time, which halves the
+// registers of the two-field case (128 -> 64) and doubles its occupancy
+template <typename T, int ND>
+__global__ void k_prolong(int bc0, int bc1, int bc2, LvlDev F, LvlDev C, const T* __restrict__ xc,
+                          T* __restrict__ xf) {
+    const int f = blockIdx.z / C.n[2];
+    int ic[3];
+    ic[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    ic[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    ic[2] = blockIdx.z - f * C.n[2];
+    if (ic[0] >= C.n[0] || ic[1] >= C.n[1]) return;
+    prolong_cell<T, 1, ND>(bc0, bc1, bc2, F, C, xc + (long long)f * C.nc, xf + (long long)f * F.nc, ic);
+}
+
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s) {
     CellLaunch cl = cell_launch(C.n);
-    MG_DISPATCH(k_prolong, cl.grid, cl.block, G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C), (const T*)C.x, (T*)F.x);
+    cl.grid.z = (unsigned)(C.n[2] * nf);
+    ++g_launch_count;
+    if (G.ndim == 3)
+        k_prolong<T, 3><<<cl.grid, cl.block, 0, s>>>(G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C), (const T*)C.x, (T*)F.x);
+    else
+        k_prolong<T, 2><<<cl.grid, cl.block, 0, s>>>(G.bc[0], G.bc[1], G.bc[2], lvl(F), lvl(C), (const T*)C.x, (T*)F.x);
 }
 template void launch_prolong<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
 template void launch_prolong<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t);
 
 template <typename T>
-__global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict__ rhs, T* __restrict__ x, int tr) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void coarsest_cell(int nf, const T* M, const T* rhs, T* x, int tr) {
     if (nf == 1) {
         x[0] = rhs[0] / M[0];
     } else {
@@ -717,12 +751,152 @@ __global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict_
 }
 
 template <typename T>
+__global__ void k_coarsest(int nf, const T* __restrict__ M, const T* __restrict__ rhs, T* __restrict__ x, int tr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    coarsest_cell<T>(nf, M, rhs, x, tr);
+}
+
+template <typename T>
 void launch_coarsest(int nf, MGLevel& C, cudaStream_t s, int tr) {
     ++g_launch_count;
     k_coarsest<T><<<1, 32, 0, s>>>(nf, (const T*)C.M, (const T*)C.rhs, (T*)C.x, tr);
 }
 template void launch_coarsest<double>(int, MGLevel&, cudaStream_t, int);
 template void launch_coarsest<float>(int, MGLevel&, cudaStream_t, int);
+
+// The coarse end of a V-cycle in one block.  Below a few thousand cells a
+// level's kernels last 4-8 us each whatever their size (launch and
+// dependency latency, about 11 launches per level), so the levels from the
+// first one at or below kTailCells down to the single-cell level run as
+// phases of one kernel separated by block barriers: the same per-cell
+// functions in the same order of phases as the separate launches (results
+// agree to rounding: the compiler may contract multiply-adds differently in
+// the two contexts).  Every phase visits its cells with a block-stride loop;
+// x, rhs and r are written and read within the kernel, so they are read
+// through plain (coherent) loads.
+struct TailLevel {
+    LvlDev L;
+    const void* M;
+    const void* K;
+    void* x;
+    void* rhs;
+    void* r;
+};
+struct TailArgs {
+    TailLevel lv[kTailMaxLevels];
+    int nlev;
+    int bc[3];
+    int nu1, nu2, tr;
+};
+
+template <typename T, int NF, int ND, bool ZS>
+__device__ __forceinline__ void tail_smooth(const TailLevel& V, int colour, int tr) {
+    const LvlDev& L = V.L;
+    const int compact = (L.n[0] % 2 == 0) ? 1 : 0;
+    const int nx = compact ? L.n[0] / 2 : L.n[0];
+    const int total = nx * L.n[1] * L.n[2];
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int t = i % nx, rem = i / nx, b = rem % L.n[1], c = rem / L.n[1];
+        const int a = compact ? 2 * t + ((b + c + colour) & 1) : t;
+        if (((a + b + c) & 1) != colour) continue;
+        smooth_cell<T, NF, ND, ZS>(L, (const T*)V.M, (const T*)V.K, (T*)V.x, (const T*)V.rhs, a, b, c, tr);
+    }
+}
+
+template <typename T, int NF, int ND>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs A) {
+    const int red_only = A.nu1 > 0 ? 1 : 0;
+    // descent: pre-smoothing (the first half sweep of every coarse level
+    // starts from zero), residual on colour 0 and restriction
+    for (int l = 0; l + 1 < A.nlev; ++l) {
+        const TailLevel& V = A.lv[l];
+        const TailLevel& W = A.lv[l + 1];
+        for (int k = 0; k < A.nu1; ++k) {
+            if (k == 0) tail_smooth<T, NF, ND, true>(V, 0, A.tr);
+            else tail_smooth<T, NF, ND, false>(V, 0, A.tr);
+            __syncthreads();
+            tail_smooth<T, NF, ND, false>(V, 1, A.tr);
+            __syncthreads();
+        }
+        {
+            const LvlDev& F = V.L;
+            const int compact = (red_only && F.n[0] % 2 == 0) ? 1 : 0;
+            const int nx = compact ? F.n[0] / 2 : F.n[0];
+            const int total = nx * F.n[1] * F.n[2];
+            for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                const int t = i % nx, rem = i / nx, b = rem % F.n[1], c = rem / F.n[1];
+                const int a = compact ? 2 * t + ((b + c) & 1) : t;
+                if (red_only && ((a + b + c) & 1)) continue;
+                residual_cell<T, NF, ND>(F, (const T*)V.M, (const T*)V.K, (const T*)V.x, (const T*)V.rhs, (T*)V.r, a,
+                                         b, c, A.tr);
+            }
+        }
+        __syncthreads();
+        {
+            const LvlDev& C = W.L;
+            const int total = C.n[0] * C.n[1] * C.n[2];
+            for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                int ic[3];
+                ic[0] = i % C.n[0];
+                ic[1] = (i / C.n[0]) % C.n[1];
+                ic[2] = i / (C.n[0] * C.n[1]);
+                restrict_cell<T, NF, ND>(V.L, C, (const T*)V.r, (T*)W.rhs, (T*)W.x, ic, lflat(C, ic[0], ic[1], ic[2]),
+                                         red_only, red_only ? 0 : 1);
+            }
+        }
+        __syncthreads();
+    }
+    const TailLevel& Z = A.lv[A.nlev - 1];
+    if (threadIdx.x == 0) coarsest_cell<T>(NF, (const T*)Z.M, (const T*)Z.rhs, (T*)Z.x, A.tr);
+    __syncthreads();
+    // ascent: prolongation and post-smoothing
+    for (int l = A.nlev - 2; l >= 0; --l) {
+        const TailLevel& V = A.lv[l];
+        const TailLevel& W = A.lv[l + 1];
+        const LvlDev& C = W.L;
+        const int total = C.n[0] * C.n[1] * C.n[2];
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            int ic[3];
+            ic[0] = i % C.n[0];
+            ic[1] = (i / C.n[0]) % C.n[1];
+            ic[2] = i / (C.n[0] * C.n[1]);
+            prolong_cell<T, NF, ND>(A.bc[0], A.bc[1], A.bc[2], V.L, C, (const T*)W.x, (T*)V.x, ic);
+        }
+        __syncthreads();
+        for (int k = 0; k < A.nu2; ++k) {
+            tail_smooth<T, NF, ND, false>(V, 1, A.tr);
+            __syncthreads();
+            tail_smooth<T, NF, ND, false>(V, 0, A.tr);
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+void launch_vcycle_tail(const Grid& G, int nf, const MGLevel* levels, int nlev, int nu1, int nu2, cudaStream_t s,
+                        int tr) {
+    TailArgs A;
+    A.nlev = nlev;
+    for (int d = 0; d < 3; ++d) A.bc[d] = G.bc[d];
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.tr = tr;
+    for (int l = 0; l < nlev; ++l) {
+        A.lv[l].L = lvl(levels[l]);
+        A.lv[l].M = levels[l].M;
+        A.lv[l].K = levels[l].K;
+        A.lv[l].x = levels[l].x;
+        A.lv[l].rhs = levels[l].rhs;
+        A.lv[l].r = levels[l].r;
+    }
+    ++g_launch_count;
+    if (nf == 1 && G.ndim == 3) k_vcycle_tail<T, 1, 3><<<1, kTailThreads, 0, s>>>(A);
+    else if (nf == 1) k_vcycle_tail<T, 1, 2><<<1, kTailThreads, 0, s>>>(A);
+    else if (G.ndim == 3) k_vcycle_tail<T, 2, 3><<<1, kTailThreads, 0, s>>>(A);
+    else k_vcycle_tail<T, 2, 2><<<1, kTailThreads, 0, s>>>(A);
+}
+template void launch_vcycle_tail<double>(const Grid&, int, const MGLevel*, int, int, int, cudaStream_t, int);
+template void launch_vcycle_tail<float>(const Grid&, int, const MGLevel*, int, int, int, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // back substitution and transform out
