@@ -768,6 +768,8 @@ def main():
     ap.add_argument("--mg-cycles", type=int, default=None, help="multigrid V-cycles per preconditioner apply")
     ap.add_argument("--mg-nu1", type=int, default=None, help="pre-smoothing sweeps")
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
+    ap.add_argument("--eta", type=float, default=None,
+                    help="GMRES relative tolerance (the paper's 1e-4 unless given)")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
     ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner", "adjoint", "machsweep"], default=None,
@@ -786,6 +788,9 @@ def main():
                     help="cells per direction of the oracle sample (--impl reference, cpu_baseline)")
     ap.add_argument("--sweep", action="store_true", help="--study tgv: GMRES iterations against CFL_hydro")
     args = ap.parse_args()
+    if args.eta is not None:
+        global ETA
+        ETA = args.eta
     for k in ("mg_cycles", "mg_nu1", "mg_nu2", "pc_freeze"):
         if getattr(args, k) is not None:
             OPT_OVERRIDES[k] = getattr(args, k)

@@ -68,6 +68,21 @@ __device__ __forceinline__ bool cell_pos(const int n[3], Idx3& P, long long& c) 
     return true;
 }
 
+// Position of this thread in tile `tile` of a cell_launch tiling (tiles in
+// x, then y, then z order), for grid-stride kernels that visit several tiles
+// per block; false outside the grid.
+__device__ __forceinline__ bool cell_pos_tile(const int n[3], int tile, Idx3& P, long long& c) {
+    const int gx = (n[0] + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int gy = (n[1] + (int)blockDim.y - 1) / (int)blockDim.y;
+    const int r = tile / gx;
+    P.i[0] = (tile - r * gx) * blockDim.x + threadIdx.x;
+    P.i[1] = (r % gy) * blockDim.y + threadIdx.y;
+    P.i[2] = r / gy;
+    if (P.i[0] >= n[0] || P.i[1] >= n[1]) return false;
+    c = ((long long)P.i[2] * n[1] + P.i[1]) * n[0] + P.i[0];
+    return true;
+}
+
 __device__ __forceinline__ int block_linear() {
     return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }

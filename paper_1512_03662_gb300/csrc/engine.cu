@@ -266,9 +266,9 @@ void precond(jfnk_handle* h, const double* X, double dt, const T* v, int vslot, 
     launch_precond_in<T>(h->G, (const T*)h->C, v, h->vscale, vslot, h->nf, (T*)h->rp, (T*)h->re, (T*)h->ru,
                          h->levels[0], s, h->opt.mg_nu1 > 0 ? 0 : 1);
     for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<T>(h, 0, 0, c == 0);
-    launch_precond_out<T>(h->G, (const T*)h->C, dt, h->nf, (const T*)h->rp, (const T*)h->re, (const T*)h->ru,
-                          h->levels[0], z, h->partials, s);
-    launch_finalize(h->partials, (int)cblocks(h), h->scal, kSlotZnorm, 0, s);
+    const int np = launch_precond_out<T>(h->G, (const T*)h->C, dt, h->nf, (const T*)h->rp, (const T*)h->re,
+                                         (const T*)h->ru, h->levels[0], z, h->partials, s);
+    launch_finalize(h->partials, np, h->scal, kSlotZnorm, 0, s);
 }
 
 // out = J^ z (basis precision), requires scaling, G0 of X

@@ -147,8 +147,8 @@ template <typename T>
 void launch_vcycle_tail(const Grid& G, int nf, const MGLevel* levels, int nlev, int nu1, int nu2, cudaStream_t s,
                         int tr);
 template <typename T>
-void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
-                        const MGLevel& L0, T* z, double* partials, cudaStream_t s);
+int launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
+                       const MGLevel& L0, T* z, double* partials, cudaStream_t s);
 
 // adjoint.cu
 // y = (a dU/dX + b dR/dX)^T w at X (p, T, chi and half mass fluxes of X precomputed);

@@ -918,15 +918,19 @@ __device__ __forceinline__ T du_at(const Grid& G, const T* C, T dt, const T* ru,
     return dt * (ru[c * nc + j] - C[(PcThf + c) * nc + j] * (dp[mg0(G, Q)] - dp[mg0(G, L)]));
 }
 
+// One wave of blocks, each visiting cell tiles with a grid stride and
+// reducing its partial |z|^2 once: with one tile per block the block-wide
+// reduction (two barriers per 128 cells) cost a quarter of the kernel.
 template <int ND, typename T>
 __global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int nf, const T* __restrict__ rp,
                               const T* __restrict__ re, const T* __restrict__ ru, const T* __restrict__ x,
-                              T* __restrict__ z, double* __restrict__ partials) {
+                              T* __restrict__ z, double* __restrict__ partials, int ntiles) {
     __shared__ double sh[32];
-    Idx3 P;
-    long long cc;
     double acc = 0.0;
-    if (cell_pos(G.n, P, cc)) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        Idx3 P;
+        long long cc;
+        if (!cell_pos_tile(G.n, tile, P, cc)) continue;
         const long long nc = G.ncell;
         const T dt = (T)dt_d;
         const long long mi = mg0(G, P);
@@ -967,17 +971,42 @@ __global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int 
         }
     }
     double s = block_sum<128>(acc, sh);
-    if (thread_linear() == 0) partials[block_linear()] = s;
+    if (thread_linear() == 0) partials[blockIdx.x] = s;
+}
+
+// blocks of one wave of k_precond_out (occupancy query, once per kernel)
+template <auto FN>
+static int one_wave(int threads) {
+    static const int g = [threads] {
+        int dev = 0, nsm = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, FN, threads, 0);
+        long long w = (long long)(nsm > 0 ? nsm : 1) * (occ > 0 ? occ : 1);
+        return (int)(w < kMaxRedBlocks ? w : kMaxRedBlocks);
+    }();
+    return g;
 }
 
 template <typename T>
-void launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
-                        const MGLevel& L0, T* z, double* partials, cudaStream_t s) {
-    CELL_LAUNCH_T(k_precond_out, T, G, C, dt, nf, rp, re, ru, (const T*)L0.x, z, partials);
+int launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp, const T* re, const T* ru,
+                       const MGLevel& L0, T* z, double* partials, cudaStream_t s) {
+    CellLaunch cl = cell_launch(G.n);
+    const long long nt = (long long)cl.grid.x * cl.grid.y * cl.grid.z;
+    const int ntiles = (int)nt;
+    int g = G.ndim == 3 ? one_wave<k_precond_out<3, T>>(cl.block.x * cl.block.y)
+                        : one_wave<k_precond_out<2, T>>(cl.block.x * cl.block.y);
+    if (g > ntiles) g = ntiles;
+    ++g_launch_count;
+    if (G.ndim == 3)
+        k_precond_out<3, T><<<g, cl.block, 0, s>>>(G, C, dt, nf, rp, re, ru, (const T*)L0.x, z, partials, ntiles);
+    else
+        k_precond_out<2, T><<<g, cl.block, 0, s>>>(G, C, dt, nf, rp, re, ru, (const T*)L0.x, z, partials, ntiles);
+    return g;
 }
-template void launch_precond_out<double>(const Grid&, const double*, double, int, const double*, const double*,
-                                         const double*, const MGLevel&, double*, double*, cudaStream_t);
-template void launch_precond_out<float>(const Grid&, const float*, double, int, const float*, const float*,
-                                        const float*, const MGLevel&, float*, double*, cudaStream_t);
+template int launch_precond_out<double>(const Grid&, const double*, double, int, const double*, const double*,
+                                        const double*, const MGLevel&, double*, double*, cudaStream_t);
+template int launch_precond_out<float>(const Grid&, const float*, double, int, const float*, const float*,
+                                       const float*, const MGLevel&, float*, double*, cudaStream_t);
 
 }  // namespace jfnk
