@@ -564,10 +564,71 @@ __global__ void k_update(double* __restrict__ x, const T* __restrict__ Z, long l
     }
 }
 
+// The same for a float basis: the products and their sum run on the FP32
+// pipe as an unevaluated pair (TwoProduct, TwoSum; each y_i split into two
+// floats), four elements per thread with 16-byte loads.  In double, the k
+// FMAs per element bound this pass by the FP64 pipe (k up to 30 at 84
+// million unknowns).  Columns of Z start on 16-byte boundaries (ld is a
+// multiple of 64) and x is 256-byte aligned; the last n mod 4 elements take
+// the scalar loop.
+__global__ void __launch_bounds__(kBlock) k_update_f32v(double* __restrict__ x, const float* __restrict__ Z,
+                                                        long long ld, int k, const double* __restrict__ y,
+                                                        long long n) {
+    __shared__ float yh[64], yl[64];
+    if (threadIdx.x < k) {
+        const double c = y[threadIdx.x];
+        const float h = (float)c;
+        yh[threadIdx.x] = h;
+        yl[threadIdx.x] = (float)(c - (double)h);
+    }
+    __syncthreads();
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = n >> 2;
+    for (long long q = t0; q < n4; q += stride) {
+        CompF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(Z + i * ld)[q];
+            const float h = yh[i], l = yl[i];
+            comp_fma(a0, h, v.x);
+            a0.e = fmaf(l, v.x, a0.e);
+            comp_fma(a1, h, v.y);
+            a1.e = fmaf(l, v.y, a1.e);
+            comp_fma(a2, h, v.z);
+            a2.e = fmaf(l, v.z, a2.e);
+            comp_fma(a3, h, v.w);
+            a3.e = fmaf(l, v.w, a3.e);
+        }
+        double2* xp = reinterpret_cast<double2*>(x) + 2 * q;
+        double2 lo = xp[0], hi = xp[1];
+        lo.x += (double)a0.s + (double)a0.e;
+        lo.y += (double)a1.s + (double)a1.e;
+        hi.x += (double)a2.s + (double)a2.e;
+        hi.y += (double)a3.s + (double)a3.e;
+        xp[0] = lo;
+        xp[1] = hi;
+    }
+    for (long long e = 4 * n4 + t0; e < n; e += stride) {
+        CompF a{0.f, 0.f};
+        for (int i = 0; i < k; ++i) {
+            const float z = Z[i * ld + e];
+            comp_fma(a, yh[i], z);
+            a.e = fmaf(yl[i], z, a.e);
+        }
+        x[e] += (double)a.s + (double)a.e;
+    }
+}
+
 template <typename T>
 void launch_update(double* x, const T* Z, long long ld, int k, const double* y, long long n, cudaStream_t s) {
     ++g_launch_count;
-    k_update<T><<<kRedBlocks, kBlock, 0, s>>>(x, Z, ld, k, y, n);
+    if (sizeof(T) == 4 && ld % 4 == 0) {
+        const int g = cached_grid<k_update_f32v>();
+        k_update_f32v<<<g, kBlock, 0, s>>>(x, (const float*)Z, ld, k, y, n);
+    } else {
+        k_update<T><<<kRedBlocks, kBlock, 0, s>>>(x, Z, ld, k, y, n);
+    }
 }
 template void launch_update<double>(double*, const double*, long long, int, const double*, long long, cudaStream_t);
 template void launch_update<float>(double*, const float*, long long, int, const double*, long long, cudaStream_t);
