@@ -271,9 +271,11 @@ void precond(jfnk_handle* h, const double* X, double dt, const T* v, int vslot, 
     launch_finalize(h->partials, np, h->scal, kSlotZnorm, 0, s);
 }
 
-// out = J^ z (basis precision), requires scaling, G0 of X
+// out = J^ z (basis precision), requires scaling, G0 of X; delta_scaled:
+// out = delta J^ z (the Arnoldi vectors of GMRES, which takes the 1/delta
+// into its Hessenberg column)
 template <typename TZ, typename T>
-void jv(jfnk_handle* h, const double* X, double dt, const TZ* z, int znorm_ready, T* out) {
+void jv(jfnk_handle* h, const double* X, double dt, const TZ* z, int znorm_ready, T* out, bool delta_scaled = false) {
     cudaStream_t s = h->stream;
     if (!znorm_ready) {
         launch_norm2_partials<TZ>(z, h->nvec, h->partials, s);
@@ -294,8 +296,12 @@ void jv(jfnk_handle* h, const double* X, double dt, const TZ* z, int znorm_ready
     if (prof) cudaEventRecord(h->ev[3], s);
     launch_mom_fluxes(h->G, h->Xp, h->Fm, h->Psi, s);
     if (prof) cudaEventRecord(h->ev[4], s);
-    launch_assemble<kModeJv, T>(h->G, h->Xp, h->p, h->Fm, h->FE, h->Psi, h->jvQ, h->jvC, h->jvP, h->scal, kSlotDelta,
-                                dt, nullptr, out, s);
+    if (delta_scaled)
+        launch_assemble<kModeJvD, T>(h->G, h->Xp, h->p, h->Fm, h->FE, h->Psi, h->jvQ, h->jvC, h->jvP, h->scal,
+                                     kSlotDelta, dt, nullptr, out, s);
+    else
+        launch_assemble<kModeJv, T>(h->G, h->Xp, h->p, h->Fm, h->FE, h->Psi, h->jvQ, h->jvC, h->jvP, h->scal,
+                                    kSlotDelta, dt, nullptr, out, s);
     if (prof) cudaEventRecord(h->ev[5], s);
 }
 
@@ -364,7 +370,7 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
                 precond<T>(h, X, dt, Vcol<T>(h, j), j, Zcol<T>(h, j));
                 t.stop();
             }
-            jv<T, T>(h, X, dt, Zcol<T>(h, j), 1, Vcol<T>(h, j + 1));
+            jv<T, T>(h, X, dt, Zcol<T>(h, j), 1, Vcol<T>(h, j + 1), true);
             {
                 Timer t(h, 8);
                 double* hcol = h->H + (long long)j * ldh;
@@ -381,7 +387,7 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
                     launch_add_col(hcol, h->hc2, j + 1, s);
                 }
                 launch_finalize(h->partials, nb, h->scal, kSlotTmp, 0, s);
-                launch_set_subdiag(h->scal, hcol, j, h->vscale, s);
+                launch_set_subdiag(h->scal, hcol, j, h->vscale, s, kSlotInvDelta);
                 launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
                 t.stop();
             }

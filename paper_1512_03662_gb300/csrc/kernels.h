@@ -8,7 +8,9 @@ namespace jfnk {
 // number of kernels launched through the launchers below (profiling aid)
 extern long long g_launch_count;
 
-enum { kModeG = 0, kModeBn = 1, kModeRes = 2, kModeNewton = 3, kModeJv = 4 };
+// kModeJvD: the Jacobian-free product times delta, L^-1 (G(X + delta R w) - G(X));
+// GMRES takes the 1/delta into its Hessenberg column instead
+enum { kModeG = 0, kModeBn = 1, kModeRes = 2, kModeNewton = 3, kModeJv = 4, kModeJvD = 5 };
 
 // device scalar slots (double array `scal` in the workspace)
 enum {
@@ -66,7 +68,10 @@ template <typename T>
 int launch_axpy_norm(T* w, const T* V, long long ld, int nv, const double* hcol, const double* vscale, long long n,
                      double* partials, cudaStream_t s);
 // hcol[j+1] = norm, vscale[j+1] = 1/norm
-void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s);
+// h_{j+1,j} = ||w|| (scal[kSlotTmp]) and the lazy scale 1/||w|| of v_{j+1};
+// with col_scale_slot >= 0 the whole column 0..j+1 is then multiplied by
+// scal[col_scale_slot] (w was formed as delta J^ z)
+void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s, int col_scale_slot = -1);
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* scal, cudaStream_t s);
 void launch_backsolve(const double* H, int ldh, int k, const double* g, double* y, cudaStream_t s);
 template <typename T>

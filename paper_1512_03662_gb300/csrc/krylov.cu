@@ -499,15 +499,22 @@ template int launch_axpy_norm<double>(double*, const double*, long long, int, co
 template int launch_axpy_norm<float>(float*, const float*, long long, int, const double*, const double*, long long,
                                      double*, cudaStream_t);
 
-__global__ void k_set_subdiag(double* scal, double* hcol, int j, double* vscale) {
+// With w = delta J^ z (kModeJvD) the Gram-Schmidt pass ran on delta times the
+// true vector: every coefficient and the norm carry the factor delta, and the
+// normalised v_{j+1} is the same, so only the Hessenberg column is rescaled.
+__global__ void k_set_subdiag(double* scal, double* hcol, int j, double* vscale, int col_scale_slot) {
     double nrm = scal[kSlotTmp];
     hcol[j + 1] = nrm;
     vscale[j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    if (col_scale_slot >= 0) {
+        const double f = scal[col_scale_slot];
+        for (int i = 0; i <= j + 1; ++i) hcol[i] *= f;
+    }
 }
 
-void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s) {
+void launch_set_subdiag(double* scal, double* hcol, int j, double* vscale, cudaStream_t s, int col_scale_slot) {
     ++g_launch_count;
-    k_set_subdiag<<<1, 1, 0, s>>>(scal, hcol, j, vscale);
+    k_set_subdiag<<<1, 1, 0, s>>>(scal, hcol, j, vscale, col_scale_slot);
 }
 
 // Column j of the Hessenberg matrix H (column-major, leading dim ldh): apply

@@ -285,9 +285,12 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         } else {
             // kModeJv: L^-1 (G(X+dw) - G(X)) / delta with bn, G0, Linv holding
             // Q = theta L^-1, C = L^-1 G(X) and P = L^-1/dt (launch_jv_coeffs):
-            // (U P - R Q - C) / delta, two FMAs and a product per unknown
+            // (U P - R Q - C) / delta, two FMAs and a product per unknown;
+            // kModeJvD leaves out the 1/delta (GMRES applies it to its
+            // Hessenberg column): two FMAs per unknown
             const double q = fma(Rv[k], bn[j], G0[j]);
-            outb[j] = wall ? (TO)0 : (TO)(fma(Uv[k], Linv[j], -q) * inv_delta);
+            const double d = fma(Uv[k], Linv[j], -q);
+            outb[j] = wall ? (TO)0 : (TO)(MODE == kModeJv ? d * inv_delta : d);
         }
     }
 }
@@ -465,6 +468,8 @@ INST(kModeNewton, double)
 INST(kModeNewton, float)
 INST(kModeJv, double)
 INST(kModeJv, float)
+INST(kModeJvD, double)
+INST(kModeJvD, float)
 #undef INST
 
 void launch_scaling(const Grid& G, const double* X, double a1, double a2, double* L, double* R, double* Linv,
