@@ -1,6 +1,6 @@
 """Parity at the full sizes of the five problems (64^2, 256^2, 128^3 at Mach
 1e-2 / 1e-4 / 1e-6, 256^3, 128^2), through the handle configuration the
-benchmark times (mixed precision; for problem 4 also its one V(2,2) cycle
+benchmark times (mixed precision; for problem 4 also its one V(1,1) cycle
 per preconditioner apply) and through the FP64 handle.
 
 One oracle residual takes about ten seconds at 256^3 on the host, so the
@@ -125,7 +125,7 @@ def test_fullsize_operators(jf, case):
     Xg, Xng = _dev(X), _dev(Xn)
     assert S.dt_from_cfl(Xng, wl.cfl_hydro) == pytest.approx(dt, rel=1e-13)
 
-    oo = J.Options(precond=wl.precond, mg_cycles=o64.mg_cycles)
+    oo = J.Options(precond=wl.precond, mg_cycles=o64.mg_cycles, mg_nu1=o64.mg_nu1, mg_nu2=o64.mg_nu2)
     sc = J.scaling(P, X, oo)
     L, R, xn = S.scaling(Xg)
     assert _relnorm(L, sc.L) < 1e-14 and _relnorm(R, sc.R) < 1e-14
