@@ -72,7 +72,7 @@ def load_peaks():
 # peak of 2 FP64 thread instructions per cycle per SM; 152 SMs at the 2070 MHz
 # maximum SM clock give 0.629 T instructions/s, 1.26 TFLOP/s with an FMA
 # counted as two flops (the nominal figure is 1.25 TFLOP/s; a DFMA
-# throughput probe on this machine measured 1.20 TFLOP/s).
+# throughput probe on a GB300 measured 1.20 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.258
 FP64_PEAK_TINST = 0.629
 

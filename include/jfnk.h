@@ -126,8 +126,8 @@ typedef struct jfnk_handle jfnk_handle;
 /* Fill *opt with the defaults listed above (precond = SOUND, FP64). */
 void jfnk_default_options(jfnk_options* opt);
 
-/* Create a solver for one grid and physics (the benchmark spec interface
- * jfnk_create(grid, eos, gravity, conductivity)).  `opt` may be NULL for the
+/* Create a solver for one grid and physics: the grid, the equation of
+ * state, gravity and conductivity of Sect. 2.  `opt` may be NULL for the
  * defaults.  Host pointers; copied.  Returns JFNK_EINVAL for unsupported
  * sizes or parameters. */
 jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_gravity* gravity,
@@ -192,7 +192,7 @@ jfnk_status jfnk_linear_solve(jfnk_handle* h, const double* X, const double* Xn,
 jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, double krylov_tol,
                       jfnk_stats* stats);
 
-/* Vector-Jacobian product of the residual (the benchmark spec's adjoint kernel;
+/* Vector-Jacobian product of the residual (the kernel of the step adjoint;
  * the paper has no adjoint): y = (dG/dX)^T w at X with G = U/dt - theta R_U,
  * i.e. the transpose of dF_U/dX of Eq. crank_nicholson.  Double vectors,
  * packed; wall slots of y are zero.  Hand-written reverse of the residual

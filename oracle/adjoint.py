@@ -1,5 +1,5 @@
-"""Adjoint of one implicit step (the benchmark spec's differentiation pattern;
-the paper has no adjoint).  TEST INFRASTRUCTURE: see the package docstring
+"""Adjoint of one implicit step (gradients through the implicit step by the
+implicit-function theorem; the paper has no adjoint).  TEST INFRASTRUCTURE: see the package docstring
 for who may import this.
 
 One step defines X^{n+1}(X^n, K0) implicitly by F(X^{n+1}; X^n, K0) = 0 with

@@ -1,6 +1,6 @@
 """Parity of the CUDA library with the float64 CPU oracle (same seeded inputs).
 
-Tolerances: the benchmark spec's bound for FP64 mode is 1e-10 relative, normwise
+Tolerances: the parity bound for FP64 mode is 1e-10 relative, normwise
 in scaled space.  Where the paper's finite-difference Jv has a noise floor
 (eps_machine |G| / (delta |Jv|)), parity is asserted at lambda = 1e-4 and only
 bounded at lambda = 1e-7.  Elementwise checks use |gpu - ref| <= rtol |ref| +
