@@ -271,7 +271,7 @@ def reference_main(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"convbox3d {args.n}^3 (problem 4)", "global_batch": 1, "seq_len": 0,
+            "config": {"workload": f"convbox3d {args.n}^3 (problem 4)",
                        "parallelism": "replicas", "l2": "state larger than L2"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"oracle implicit step at {n_small}^3 (same construction, same dt), "
@@ -936,7 +936,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64 residual / f32 Krylov",
                 "data": "synthetic",
                 "config": {"workload": f"convbox3d {args.n}^3 (problem 4), CFL_hydro {wl.cfl_hydro:g}, "
-                                       f"dt {dt:.4g}", "global_batch": 1, "seq_len": 0,
+                                       f"dt {dt:.4g}",
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "state (670 MB/vector) larger than L2, no flush", "solver": solver_cfg},
                 "jv_gcell_s": njv * wl.ncell / (jv_ms / 1e3) / 1e9 if jv_ms > 0 else None,
