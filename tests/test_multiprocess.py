@@ -8,6 +8,8 @@ import socket
 import subprocess
 import sys
 
+import pytest
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -56,3 +58,13 @@ def test_reference_arm_runs_on_rank_zero_only():
     d = json.loads(lines0[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the line carries the keys of the benchmark's JSON contract
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["n_gpus"] == 2 and d["steps"] == 1 and d["higher_is_better"] is True
+    assert d["ms_per_step"] == pytest.approx(1e3 / d["value"], rel=1e-9)
+    assert "workload" in d["config"] and not {"model", "global_batch", "seq_len"} & set(d["config"])
+    cb = d["cpu_baseline"]
+    assert cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["d2h_bytes_per_step"] == 0
