@@ -11,7 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "jfnk.h")).read()
+    with open(os.path.join(ROOT, "include", "jfnk.h")) as f:
+        src = f.read()
     return sorted(set(re.findall(r"\b(jfnk_[a-z_]+)\s*\(", src)))
 
 
