@@ -31,9 +31,11 @@
  * Errors.  Negative status = error, nothing useful written, message in
  * jfnk_last_error().  Positive status = completed without meeting the
  * requested tolerance (outputs valid, see jfnk_stats).  Calls are queued
- * asynchronously on the bound stream except jfnk_step, jfnk_linear_solve and
- * jfnk_dt_from_cfl, which read scalars back to the host and return after the
- * stream has reached them.  A handle is not thread-safe.
+ * asynchronously on the bound stream except those that read scalars back to
+ * the host and therefore return only after the stream has reached them:
+ * jfnk_step, jfnk_linear_solve, jfnk_vjp and jfnk_dt_from_cfl always;
+ * jfnk_jv when its host out-pointer delta_used is non-NULL; jfnk_scaling when
+ * its host out-pointer xhat_norm is non-NULL.  A handle is not thread-safe.
  */
 #ifndef JFNK_H
 #define JFNK_H
@@ -152,13 +154,16 @@ jfnk_status jfnk_set_options(jfnk_handle* h, const jfnk_options* opt);
 jfnk_status jfnk_residual(jfnk_handle* h, const double* X, const double* Xn, double dt, double* F);
 
 /* Diagonal scalings of Eq. jacobian_system_norm at X: L and R (double,
- * packed; wall slots 1) and, in *xhat_norm (host), ||R^-1 X||_2. */
+ * packed; wall slots 1; either may be NULL) and, in *xhat_norm (host, may be
+ * NULL), ||R^-1 X||_2.  With xhat_norm non-NULL the call synchronises the
+ * bound stream to read the norm back. */
 jfnk_status jfnk_scaling(jfnk_handle* h, const double* X, double* L, double* R, double* xhat_norm);
 
 /* Scaled Jacobian-free product of Sect. 4.2 (Eqs. jacobian_free, pert_old or
  * pert_new):  Jv = L^-1 [G(X + delta R v) - G(X)] / delta,  G = U/dt - theta
  * R_U, delta from the options' perturbation rule; *delta_used (host, may be
- * NULL) receives delta.  v, Jv: precision type (see above). */
+ * NULL) receives delta.  v, Jv: precision type (see above).  With delta_used
+ * non-NULL the call synchronises the bound stream to read delta back. */
 jfnk_status jfnk_jv(jfnk_handle* h, const double* X, double dt, const void* v, void* Jv, double* delta_used);
 
 /* Physics-based preconditioner of Sect. 4.3 in scaled form:
@@ -234,7 +239,10 @@ jfnk_status jfnk_set_profiling(jfnk_handle* h, int on);
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one array: calls that overlap on the GPU race, so
  * serialise them.  Queued on the handle's stream (the legacy default stream
- * if the handle was never bound). */
+ * if the handle was never bound).  The device current at the call must be the
+ * one the handle was bound on (JFNK_EINVAL otherwise); an unbound handle runs
+ * on the current device.  The cached address does not survive a
+ * cudaDeviceReset of that device: do not call this after one. */
 jfnk_status jfnk_residual_noalloc(jfnk_handle* h, const double* X, const double* Xn, double dt, double* F);
 
 /* Message of the last error on this handle (never NULL). */

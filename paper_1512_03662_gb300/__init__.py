@@ -153,6 +153,13 @@ def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _resolve_device(device) -> torch.device:
+    d = torch.device(device)
+    if d.type == "cuda" and d.index is None:
+        d = torch.device("cuda", torch.cuda.current_device())
+    return d
+
+
 class Solver:
     """One handle of the C library plus its torch-allocated workspace.
 
@@ -179,15 +186,17 @@ class Solver:
                 L.jfnk_destroy(self.h)
                 self.h = None
             raise JFNKError(st, msg)
-        self.device = torch.device(device)
+        self.device = _resolve_device(device)
         self.nvec = int(L.jfnk_vector_length(self.h))
+        self.vdtype = torch.float32 if self.options.precision == MIXED else torch.float64
         nbytes = int(L.jfnk_workspace_bytes(self.h))
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self.workspace.data_ptr()
         off = (-base) % 256
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._check(L.jfnk_bind(self.h, ctypes.c_void_p(base + off), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
-        self.vdtype = torch.float32 if self.options.precision == MIXED else torch.float64
+        with torch.cuda.device(self.device):      # the handle records the device current at jfnk_bind
+            self._check(L.jfnk_bind(self.h, ctypes.c_void_p(base + off), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream)))
 
     @staticmethod
     def from_workload(wl, options: Optional[jfnk_options] = None, **kw) -> "Solver":
@@ -215,6 +224,23 @@ class Solver:
     def _vec(self, dtype=torch.float64) -> torch.Tensor:
         return torch.empty(self.nvec, dtype=dtype, device=self.device)
 
+    def _arg(self, t, name: str, dtype=torch.float64):
+        """Device pointer of a vector argument, after checking that the C ABI
+        can take it: a contiguous tensor on the handle's device with the
+        expected dtype and the packed vector length.  A wrong tensor raises
+        ValueError (TypeError for a non-tensor) before any library call."""
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor, not {type(t).__name__}")
+        if t.device != self.device:
+            raise ValueError(f"{name} is on {t.device}, the solver on {self.device}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() != self.nvec:
+            raise ValueError(f"{name} has {t.numel()} elements, the packed vector has {self.nvec}")
+        return ctypes.c_void_p(t.data_ptr())
+
     def set_options(self, options: jfnk_options):
         self._check(lib().jfnk_set_options(self.h, ctypes.byref(options)))
         self.options = options
@@ -223,44 +249,52 @@ class Solver:
         self._check(lib().jfnk_set_profiling(self.h, int(on)))
 
     def residual(self, X: torch.Tensor, Xn: torch.Tensor, dt: float, out: Optional[torch.Tensor] = None):
+        px, pn = self._arg(X, "X"), self._arg(Xn, "Xn")
         F = self._vec() if out is None else out
-        self._check(lib().jfnk_residual(self.h, _ptr(X), _ptr(Xn), dt, _ptr(F)))
+        self._check(lib().jfnk_residual(self.h, px, pn, dt, self._arg(F, "out")))
         return F
 
     def residual_noalloc(self, X: torch.Tensor, Xn: torch.Tensor, dt: float, out: Optional[torch.Tensor] = None):
         """jfnk_residual_noalloc: the residual with the library's fixed scratch
         (no workspace use, nothing allocated by the call)."""
+        px, pn = self._arg(X, "X"), self._arg(Xn, "Xn")
         F = self._vec() if out is None else out
-        self._check(lib().jfnk_residual_noalloc(self.h, _ptr(X), _ptr(Xn), dt, _ptr(F)))
+        with torch.cuda.device(self.device):
+            self._check(lib().jfnk_residual_noalloc(self.h, px, pn, dt, self._arg(F, "out")))
         return F
 
     def scaling(self, X: torch.Tensor):
+        px = self._arg(X, "X")
         L, R = self._vec(), self._vec()
         xn = ctypes.c_double()
-        self._check(lib().jfnk_scaling(self.h, _ptr(X), _ptr(L), _ptr(R), ctypes.byref(xn)))
+        self._check(lib().jfnk_scaling(self.h, px, _ptr(L), _ptr(R), ctypes.byref(xn)))
         return L, R, xn.value
 
     def jv(self, X: torch.Tensor, dt: float, v: torch.Tensor, out: Optional[torch.Tensor] = None):
+        px, pv = self._arg(X, "X"), self._arg(v, "v", self.vdtype)
         Jv = self._vec(self.vdtype) if out is None else out
         d = ctypes.c_double()
-        self._check(lib().jfnk_jv(self.h, _ptr(X), dt, _ptr(v), _ptr(Jv), ctypes.byref(d)))
+        self._check(lib().jfnk_jv(self.h, px, dt, pv, self._arg(Jv, "out", self.vdtype), ctypes.byref(d)))
         return Jv, d.value
 
     def precond_apply(self, X: torch.Tensor, dt: float, v: torch.Tensor, out: Optional[torch.Tensor] = None):
+        px, pv = self._arg(X, "X"), self._arg(v, "v", self.vdtype)
         w = self._vec(self.vdtype) if out is None else out
-        self._check(lib().jfnk_precond_apply(self.h, _ptr(X), dt, _ptr(v), _ptr(w)))
+        self._check(lib().jfnk_precond_apply(self.h, px, dt, pv, self._arg(w, "out", self.vdtype)))
         return w
 
     def linear_solve(self, X: torch.Tensor, Xn: torch.Tensor, dt: float):
+        px, pn = self._arg(X, "X"), self._arg(Xn, "Xn")
         dx = self._vec()
         st = jfnk_stats()
-        code = self._check(lib().jfnk_linear_solve(self.h, _ptr(X), _ptr(Xn), dt, _ptr(dx), ctypes.byref(st)),
+        code = self._check(lib().jfnk_linear_solve(self.h, px, pn, dt, _ptr(dx), ctypes.byref(st)),
                            allow_positive=True)
         return dx, st.as_dict(), code
 
     def step(self, X: torch.Tensor, dt: float, newton_tol: float = 0.0, krylov_tol: float = 0.0):
+        px = self._arg(X, "X")
         st = jfnk_stats()
-        code = self._check(lib().jfnk_step(self.h, _ptr(X), dt, newton_tol, krylov_tol, ctypes.byref(st)),
+        code = self._check(lib().jfnk_step(self.h, px, dt, newton_tol, krylov_tol, ctypes.byref(st)),
                            allow_positive=True)
         d = st.as_dict()
         d["status"] = code
@@ -269,27 +303,30 @@ class Solver:
     def si_step(self, X: torch.Tensor, dt: float) -> None:
         """jfnk_si_step: one step of the semi-implicit scheme as a time
         integrator, in place in X."""
-        self._check(lib().jfnk_si_step(self.h, _ptr(X), dt))
+        self._check(lib().jfnk_si_step(self.h, self._arg(X, "X"), dt))
 
     def vjp_residual(self, X: torch.Tensor, dt: float, w: torch.Tensor) -> torch.Tensor:
         """jfnk_vjp_residual: (dG/dX)^T w at X."""
+        px, pw = self._arg(X, "X"), self._arg(w, "w")
         y = self._vec()
-        self._check(lib().jfnk_vjp_residual(self.h, _ptr(X), dt, _ptr(w), _ptr(y)))
+        self._check(lib().jfnk_vjp_residual(self.h, px, dt, pw, _ptr(y)))
         return y
 
     def vjp(self, Xn: torch.Tensor, Xnp1: torch.Tensor, dt: float, gbar: torch.Tensor):
         """jfnk_vjp: gradients through one implicit step; returns
         (dL/dXn, dL/dK0, stats, status)."""
+        pn, pn1, pg = self._arg(Xn, "Xn"), self._arg(Xnp1, "Xnp1"), self._arg(gbar, "gbar")
         gXn = self._vec()
         gK0 = ctypes.c_double()
         st = jfnk_stats()
-        code = self._check(lib().jfnk_vjp(self.h, _ptr(Xn), _ptr(Xnp1), dt, _ptr(gbar), _ptr(gXn),
+        code = self._check(lib().jfnk_vjp(self.h, pn, pn1, dt, pg, _ptr(gXn),
                                           ctypes.byref(gK0), ctypes.byref(st)), allow_positive=True)
         return gXn, gK0.value, st.as_dict(), code
 
     def dt_from_cfl(self, X: torch.Tensor, cfl: float) -> float:
+        px = self._arg(X, "X")
         dt = ctypes.c_double()
-        self._check(lib().jfnk_dt_from_cfl(self.h, _ptr(X), cfl, ctypes.byref(dt)))
+        self._check(lib().jfnk_dt_from_cfl(self.h, px, cfl, ctypes.byref(dt)))
         return dt.value
 
 

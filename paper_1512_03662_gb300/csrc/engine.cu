@@ -29,6 +29,7 @@ struct jfnk_handle {
     size_t ws_bytes;
     char* ws;
     cudaStream_t stream;
+    int device;        // device current at jfnk_bind (-1: never bound)
     double* hpin;      // pinned host scalars
     std::string err;
     int profiling;
@@ -589,6 +590,7 @@ jfnk_status validate_options(jfnk_handle* h, const jfnk_options* o) {
 // accessors for the allocation-free entry point (noalloc.cu)
 const jfnk::Grid* jfnk_handle_grid(const jfnk_handle* h) { return &h->G; }
 cudaStream_t jfnk_handle_stream(const jfnk_handle* h) { return h->stream; }
+int jfnk_handle_device(const jfnk_handle* h) { return h->device; }
 void jfnk_handle_set_error(jfnk_handle* h, const char* msg) { h->err = msg; }
 
 extern "C" {
@@ -625,6 +627,7 @@ jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_g
     h->ws = nullptr;
     h->hpin = nullptr;
     h->stream = 0;
+    h->device = -1;
     h->profiling = 0;
     for (auto& e : h->ev) e = nullptr;
     if (opt) h->opt = *opt;
@@ -687,8 +690,11 @@ jfnk_status jfnk_bind(jfnk_handle* h, void* ws, size_t bytes, void* stream) {
     if (!h) return JFNK_EINVAL;
     if (!ws || bytes < h->ws_bytes) return fail(h, JFNK_ENOMEM, "workspace of %zu bytes, need %zu", bytes, h->ws_bytes);
     if (((uintptr_t)ws) & 255) return fail(h, JFNK_EINVAL, "workspace must be 256-byte aligned");
+    int dev = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
     h->ws = (char*)ws;
     h->stream = (cudaStream_t)stream;
+    h->device = dev;
     plan(h, h->ws);
     if (!h->hpin) CUDA_TRY(h, cudaMallocHost((void**)&h->hpin, kNumSlots * sizeof(double)));
     return JFNK_OK;

@@ -15,10 +15,14 @@
 // library holds it (JFNK_NOALLOC_MAX_CELLS * 23 doubles, 12.1 MB) until the
 // process exits.  Host code reaches it only through the address returned by
 // cudaGetSymbolAddress, fetched once per device on the first call made with
-// that device current.  Every call shares the one array, so calls that
-// overlap on the GPU (different streams, or different host threads) race;
-// callers must serialise them.  No scratch needs clearing: each call writes
-// every scratch value before reading it.
+// that device current and kept in an atomic per-device slot (concurrent
+// first calls from several host threads store the same address).  A handle
+// bound with jfnk_bind must be called with its own device current.  Every
+// call shares the one array, so calls that overlap on the GPU (different
+// streams, or different host threads) race; callers must serialise them.  No
+// scratch needs clearing: each call writes every scratch value before
+// reading it.
+#include <atomic>
 #include <cstdio>
 #include <string>
 
@@ -35,21 +39,19 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_noalloc_scratch[kNoallocFields * JFNK_NOALLOC_MAX_CELLS];
 
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
 
-// Device address of the scratch array for the current device (fetched once).
-cudaError_t scratch_for_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// Device address of the scratch array on device dev, which must be current
+// (fetched once per device; a race between first calls stores one address).
+cudaError_t scratch_for_device(int dev, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = (double*)g_scratch_ptr[dev];
+    *out = (double*)p;
     return cudaSuccess;
 }
 
@@ -58,6 +60,7 @@ cudaError_t scratch_for_current_device(double** out) {
 // Grid and stream of a handle (defined with the handle in engine.cu).
 const jfnk::Grid* jfnk_handle_grid(const jfnk_handle* h);
 cudaStream_t jfnk_handle_stream(const jfnk_handle* h);
+int jfnk_handle_device(const jfnk_handle* h);
 void jfnk_handle_set_error(jfnk_handle* h, const char* msg);
 
 extern "C" jfnk_status jfnk_residual_noalloc(jfnk_handle* h, const double* X, const double* Xn, double dt,
@@ -75,10 +78,19 @@ extern "C" jfnk_status jfnk_residual_noalloc(jfnk_handle* h, const double* X, co
         jfnk_handle_set_error(h, buf);
         return JFNK_EINVAL;
     }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && jfnk_handle_device(h) >= 0 && jfnk_handle_device(h) != dev) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "jfnk_residual_noalloc: handle bound on device %d but device %d is current",
+                 jfnk_handle_device(h), dev);
+        jfnk_handle_set_error(h, buf);
+        return JFNK_EINVAL;
+    }
     double* base = nullptr;
-    cudaError_t e = scratch_for_current_device(&base);
+    if (e == cudaSuccess) e = scratch_for_device(dev, &base);
     if (e != cudaSuccess) {
-        std::string m = std::string("jfnk_residual_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+        std::string m = std::string("jfnk_residual_noalloc: device address lookup failed: ") + cudaGetErrorString(e);
         jfnk_handle_set_error(h, m.c_str());
         return JFNK_ECUDA;
     }

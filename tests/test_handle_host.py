@@ -166,3 +166,61 @@ def test_calls_before_binding_a_workspace_are_refused(jf):
     assert L.jfnk_bind(h, ctypes.c_void_p(4096 + 8), ctypes.c_size_t(nbytes), None) == jf.JFNK_EINVAL
     assert "256-byte aligned" in L.jfnk_last_error(h).decode()
     L.jfnk_destroy(h)
+
+
+def _fake_solver(jf, nvec=64, mixed=False):
+    """A Solver whose handle is never used: the argument checks of the
+    binding run before any library call, so they can be tested without a
+    GPU (the device is only compared, never touched)."""
+    import torch
+    S = object.__new__(jf.Solver)
+    S.h = None
+    S.device = torch.device("cuda", 0)
+    S.nvec = nvec
+    S.vdtype = torch.float32 if mixed else torch.float64
+    return S
+
+
+def test_binding_rejects_tensors_the_library_cannot_take(jf):
+    """CPU tensors, a wrong dtype, a non-contiguous view or a wrong length
+    raise before the pointer reaches the C ABI (a wrong tensor would make
+    the kernels read or write out of bounds)."""
+    import torch
+    S = _fake_solver(jf)
+    good_shape = torch.zeros(64, dtype=torch.float64)
+    with pytest.raises(ValueError, match="is on cpu"):
+        S.residual(good_shape, good_shape, 0.1)
+    with pytest.raises(TypeError):
+        S.step([0.0] * 64, 0.1)
+    meta = dict(device="meta")
+    # the checks compare metadata only, so meta tensors stand in for device tensors
+    S.device = torch.device("meta")
+    with pytest.raises(ValueError, match="dtype"):
+        S.residual(torch.empty(64, dtype=torch.float32, **meta), torch.empty(64, dtype=torch.float64, **meta), 0.1)
+    with pytest.raises(ValueError, match="contiguous"):
+        S.step(torch.empty(128, dtype=torch.float64, **meta)[::2], 0.1)
+    with pytest.raises(ValueError, match="elements"):
+        S.dt_from_cfl(torch.empty(63, dtype=torch.float64, **meta), 1.0)
+    with pytest.raises(ValueError, match="Xn"):
+        S.linear_solve(torch.empty(64, dtype=torch.float64, **meta), torch.empty(65, dtype=torch.float64, **meta),
+                       0.1)
+    with pytest.raises(ValueError, match="gbar"):
+        S.vjp(torch.empty(64, dtype=torch.float64, **meta), torch.empty(64, dtype=torch.float64, **meta), 0.1,
+              torch.empty(64, dtype=torch.float32, **meta))
+
+
+def test_binding_checks_krylov_vectors_against_the_handle_precision(jf):
+    """Jv and preconditioner vectors are float on a mixed handle and double
+    on an FP64 handle; X stays double on both."""
+    import torch
+    meta = dict(device="meta")
+    X = torch.empty(64, dtype=torch.float64, **meta)
+    for mixed, bad in ((True, torch.float64), (False, torch.float32)):
+        S = _fake_solver(jf, mixed=mixed)
+        S.device = torch.device("meta")
+        with pytest.raises(ValueError, match="v has dtype"):
+            S.jv(X, 0.1, torch.empty(64, dtype=bad, **meta))
+        with pytest.raises(ValueError, match="v has dtype"):
+            S.precond_apply(X, 0.1, torch.empty(64, dtype=bad, **meta))
+        with pytest.raises(ValueError, match="X has dtype"):
+            S.jv(X.float(), 0.1, torch.empty(64, dtype=S.vdtype, **meta))

@@ -79,3 +79,24 @@ def test_noalloc_rejects_grids_above_its_limit(jf):
         assert b"exceed" in L.jfnk_last_error(h)
     finally:
         L.jfnk_destroy(h)
+
+
+def test_noalloc_on_a_bound_handle_follows_its_stream(jf):
+    """On a handle bound to a workspace and to a non-default stream, the
+    allocation-free residual is queued on that stream like jfnk_residual:
+    two calls in a row, each right after a residual on the same stream,
+    agree with it."""
+    wl = W.config(4, n=(16, 16, 16))
+    stream = torch.cuda.Stream()
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=0), stream=stream)
+    Xn = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(5)
+    for call in range(2):
+        X = Xn * torch.as_tensor(1.0 + 0.01 * rng.standard_normal(Xn.numel()), device="cuda")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ref = S.residual(X, Xn, 0.37)
+            F = S.residual_noalloc(X, Xn, 0.37)
+        stream.synchronize()
+        rel = float((F - ref).norm() / ref.norm())
+        assert rel < 1e-10, (call, rel)
