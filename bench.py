@@ -44,6 +44,9 @@ ETA = 1e-4
 # jv_kernels_128cubed.md): flops = dadd + dmul + 2 dfma, instructions =
 # dadd + dmul + dfma, both divided by the cell count.  Division sequences are
 # counted as the DFMA/DMUL/DADD instructions they execute.
+# KERNEL_COUNTS_HASH is kernel_source_hash() of the sources those counts were
+# measured on.
+KERNEL_COUNTS_HASH = "0b523195db698bf9"
 FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 6.0, "face_fluxes": 85.0, "mom_fluxes": 120.0, "assemble": 97.9}
 FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 71.0, "mom_fluxes": 96.0, "assemble": 65.9}
 # DRAM bytes per cell per launch from the same capture (dram__bytes_read +
@@ -68,13 +71,66 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-# FP64 peak of GB300 from its unit counts and clock: ncu reports a sustained
-# peak of 2 FP64 thread instructions per cycle per SM; 152 SMs at the 2070 MHz
-# maximum SM clock give 0.629 T instructions/s, 1.26 TFLOP/s with an FMA
-# counted as two flops (the nominal figure is 1.25 TFLOP/s; a DFMA
-# throughput probe on a GB300 measured 1.20 TFLOP/s).
+# FP64 peak of GB300 from its unit counts and clock, used only when the
+# probe below cannot run: ncu reports a sustained peak of 2 FP64 thread
+# instructions per cycle per SM; 152 SMs at the 2070 MHz maximum SM clock give
+# 0.629 T instructions/s, 1.26 TFLOP/s with an FMA counted as two flops.
 FP64_PEAK_TFLOPS = 1.258
 FP64_PEAK_TINST = 0.629
+
+
+def kernel_source_hash() -> str:
+    """Hash of the sources of the Jv kernels whose ncu instruction counts are
+    recorded above; the roofline object flags the counts as stale when the
+    sources no longer match the hash they were measured at."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("residual.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1512_03662_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def fp64_probe(device, stream, reps=5):
+    """Measured FP64 issue rate of this GPU: a grid of 8 resident 256-thread
+    blocks per SM, each thread running eight independent DFMA chains
+    (libfp64probe.so), timed with CUDA events on `stream`; returns the best
+    of `reps` launches in T instructions/s (a DFMA is one instruction and two
+    flops) with the clocks sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    lib = ctypes.CDLL(B.PROBE_LIB)
+    lib.fp64_probe_launch.restype = ctypes.c_int
+    lib.fp64_probe_launch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    lib.fp64_probe_fma_per_thread.restype = ctypes.c_longlong
+    lib.fp64_probe_fma_per_thread.argtypes = [ctypes.c_int]
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, iters = sms * 8, 16384
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=device)
+    ptr, sp = ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream)
+    for _ in range(2):
+        if lib.fp64_probe_launch(ptr, blocks, iters, 0.999, sp) != 0:
+            raise RuntimeError("FP64 probe launch failed")
+    clocks = ClockSampler(device.index or 0)
+    clocks.start()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            lib.fp64_probe_launch(ptr, blocks, iters, 0.999, sp)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    if not bool(torch.isfinite(out).all()):
+        raise RuntimeError("FP64 probe produced non-finite values")
+    inst = blocks * 256 * lib.fp64_probe_fma_per_thread(iters)
+    best = min(times)
+    return {"tinst_s": inst / (best / 1e3) / 1e12, "tflops": 2 * inst / (best / 1e3) / 1e12,
+            "ms_best": best, "ms_median": statistics.median(times), "launches": reps, "sms": sms,
+            "dfma_per_launch": inst, "clocks": clk}
 
 
 class ClockSampler:
@@ -176,6 +232,15 @@ OPT_OVERRIDES = {"mg_cycles": 1, "mg_nu1": 1, "mg_nu2": 1}
 # the options given on the command line alone (the studies otherwise use the
 # library defaults)
 CLI_OPTS = {}
+# lambda of the extra arm of the benchmark line.  At lambda = 1e-7 (Sect.
+# 5.1.1) the first-order truncation error of the Jacobian-free quotient
+# limits the late Newton iterations of this workload (about 1e-2 of the
+# linear residual: see tests/test_oracle_newton_convergence.py).  Eq.
+# pert_old makes delta grow with ||R^-1 X||, i.e. with the square root of
+# the number of unknowns, so the perturbation the paper tuned at 64^3 is
+# reached at 256^3 with lambda = 1e-7 (64/256)^(3/2) = 1.25e-8; the arm
+# reports the step rate with that lambda beside the headline.
+LAM_ARM = 1.25e-8
 
 
 def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
@@ -224,22 +289,33 @@ def e2e_arm(jf, wl, precision, steps, warmup, device, stream):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    stats = []
     with torch.cuda.stream(stream):
         e0.record(stream)
         for _ in range(steps):
             X.copy_(host, non_blocking=True)
-            S.step(X, dt, NEWTON_TOL, ETA)
+            stats.append(S.step(X, dt, NEWTON_TOL, ETA))
             host.copy_(X, non_blocking=True)
         e1.record(stream)
     torch.cuda.synchronize()
     nbytes = host.numel() * 8
-    return e0.elapsed_time(e1), nbytes
+    return e0.elapsed_time(e1), nbytes, stats
 
 
-def oracle_sample(n_small=32, steps=1):
+def convergence(stats) -> dict:
+    """Counts over the timed steps: steps that met the Newton tolerance,
+    steps stopped at newton_max, and linear solves stopped at gmres_max_it."""
+    return {"steps_converged": sum(1 for s in stats if s["converged"]),
+            "steps_timed": len(stats),
+            "newton_capped": sum(1 for s in stats if not s["converged"]),
+            "gmres_capped": sum(1 - c for s in stats for c in s["gmres_converged"]),
+            "linear_solves": sum(s["newton_iterations"] for s in stats)}
+
+
+def oracle_sample(n_small=32, steps=1, with_stats=False):
     """The CPU oracle as it stands: implicit steps of the same construction at
     n_small^3 with the same physical dt and solver settings; returns (s per
-    step, threads)."""
+    step, threads) and, with with_stats, the Newton and GMRES counts."""
     import torch
     from oracle import discretization as D
     from oracle import jfnk as J
@@ -248,10 +324,74 @@ def oracle_sample(n_small=32, steps=1):
     dt = D.cfl_dt(P, wl.X0, wl.cfl_hydro)
     X = torch.as_tensor(wl.X0)
     t0 = time.perf_counter()
+    st = None
     for _ in range(steps):
         X, st = J.newton_step(P, X, dt, J.Options(precond=wl.precond, newton_tol=NEWTON_TOL, eta=ETA,
                                                    **OPT_OVERRIDES))
-    return (time.perf_counter() - t0) / steps, torch.get_num_threads()
+    sec = (time.perf_counter() - t0) / steps
+    if with_stats:
+        return sec, torch.get_num_threads(), {"newton_iterations": st.newton_iterations,
+                                              "gmres_iterations": list(st.gmres_iterations),
+                                              "converged": bool(st.converged)}
+    return sec, torch.get_num_threads()
+
+
+def cpu_info() -> dict:
+    """Host CPU: logical core count and model name (lscpu, else /proc/cpuinfo)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    return {"logical_cores": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def oracle_kernels(wl, threads: int, reps: int) -> dict:
+    """The oracle's residual F(X; X^n) (two evaluations of R_U, as
+    jfnk_residual) and one Jacobian-free product (one evaluation of G, G(X)
+    precomputed as in GMRES) on the workload itself, `reps` calls each with
+    `threads` torch threads: median seconds and cells per second."""
+    import torch
+    from oracle import discretization as D
+    from oracle import jfnk as J
+    import workloads as W
+    old = torch.get_num_threads()
+    torch.set_num_threads(threads)
+    try:
+        P = D.Problem.from_workload(wl)
+        X = torch.as_tensor(wl.X0)
+        dt = D.cfl_dt(P, X, wl.cfl_hydro)
+        tr = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            D.residual(P, X, X, dt)
+            tr.append(time.perf_counter() - t0)
+        o = J.Options(precond=wl.precond)
+        sc = J.scaling(P, X, o)
+        G0 = D.G_operator(P, X, dt)
+        v = torch.as_tensor(W.random_vector(wl, 3))
+        tj = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            J.jv(P, X, G0, sc, v, dt, o)
+            tj.append(time.perf_counter() - t0)
+        del sc, G0, v
+    finally:
+        torch.set_num_threads(old)
+    mr, mj = statistics.median(tr), statistics.median(tj)
+    return {"threads": threads, "calls": reps, "residual_s": mr, "jv_s": mj,
+            "residual_gcell_s": wl.ncell / mr / 1e9, "jv_gcell_s": wl.ncell / mj / 1e9}
 
 
 def reference_main(args, ws, rank):
@@ -563,12 +703,17 @@ def study_vortex(args):
 
 def study_inner(args):
     """--study inner: accuracy of the inner SI solve (the paper's eta' of
-    Sect. 3.5, here the number of V-cycles: about 0.1 residual reduction
-    each, so 1, 2, 4, 8 cycles stand for eta' ~ 1e-1, 1e-2, 1e-4, 1e-8) and
-    SI coefficients from each Newton iterate or frozen at X^n, on the
-    Taylor-Green vortex 64^3 (M = 1e-2, 1e-4, CFL_adv = 0.5, after 100 steps
-    at CFL_hydro = 1) and on problem 2 at 256^2 (conduction, CFL 100):
-    GMRES iterations per Newton iteration and step rate."""
+    Sect. 3.5, which the paper leaves for future investigation, noting that
+    eta' <= 1e-6 behaves like a direct solve) and SI coefficients from each
+    Newton iterate or frozen at X^n, on the Taylor-Green vortex 64^3 (M =
+    1e-2, 1e-4, CFL_adv = 0.5, after 100 steps at CFL_hydro = 1), problem 2
+    at 256^2 (conduction, CFL 100) and problem 4 at --n^3 (default 128^3,
+    the benchmark's time step).  Arms: a fixed number of V-cycles per apply
+    (1, 2, 4) with the inner residual measured after every apply, and V-cycles
+    repeated until the measured relative residual reaches eta' = 1e-2, 1e-4,
+    1e-6 or 1e-10 ("direct").  Reports GMRES iterations per Newton
+    iteration, V-cycles per apply, the measured eta' (mean and maximum over
+    the applies) and the step rate."""
     import torch
     from paper_1512_03662_gb300 import build as B
     B.build()
@@ -585,36 +730,96 @@ def study_inner(args):
             S.step(X, dt1, NEWTON_TOL, ETA)
         dt = 0.5 * (2.0 * math.pi / 64) / tgv_speed_max(X, wl.ncell)
         cases.append((f"tgv64 M={mach:g}", wl, X.clone(), dt))
+        del S
     wl = W.config(2)
     X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
     S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec))
     cases.append(("problem2 256^2", wl, X, S.dt_from_cfl(X, wl.cfl_hydro)))
+    del S
+    n4 = args.study_n or 128
+    wl = make_workload(n4)
+    X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec))
+    cases.append((f"problem4 {n4}^3", wl, X, S.dt_from_cfl(X, wl.cfl_hydro)))
+    del S
+    arms = [(f"fixed {c} V({nu},{nu})", {"mg_cycles": c, "mg_nu1": nu, "mg_nu2": nu, "inner_monitor": 1})
+            for c, nu in ((1, 1), (1, 2), (2, 2), (4, 2))]
+    arms += [(f"eta' {tol:g}", {"inner_tol": tol, "inner_max_cycles": 60}) for tol in (1e-2, 1e-4, 1e-6, 1e-10)]
+    arms += [("fixed 1 V(2,2), frozen at X^n", {"mg_cycles": 1, "pc_freeze": 1, "inner_monitor": 1})]
     for name, wl, X0, dt in cases:
-        for cycles in (1, 2, 4, 8):
-            for freeze in (0, 1):
-                o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, mg_cycles=cycles,
-                                       pc_freeze=freeze)
-                S = jf.Solver.from_workload(wl, o)
-                X = X0.clone()
-                nn = ng = 0
-                err = None
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                k = 0
-                for k in range(args.steps):
-                    try:
-                        st = S.step(X, dt, NEWTON_TOL, ETA)
-                    except jf.JFNKError as e:
-                        err = str(e)
-                        break
-                    nn += st["newton_iterations"]
-                    ng += st["gmres_iterations_total"]
-                torch.cuda.synchronize()
-                el = time.perf_counter() - t0
-                print(json.dumps({"study": "inner", "case": name, "mg_cycles": cycles, "pc_freeze": freeze,
-                                  "steps": args.steps, "steps_per_s": args.steps / el if err is None else None,
-                                  "newton_per_step": nn / max(1, k + (err is None)),
-                                  "gmres_per_newton": ng / max(1, nn), "error": err}), flush=True)
+        for arm, kw in arms:
+            o = jf.default_options(**{"theta": wl.theta, "precond": wl.precond, "precision": prec, **kw})
+            S = jf.Solver.from_workload(wl, o)
+            X = X0.clone()
+            nn = ng = napp = ncyc = 0
+            emean, emax, err = [], 0.0, None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            k = 0
+            for k in range(args.steps):
+                try:
+                    st = S.step(X, dt, NEWTON_TOL, ETA)
+                except jf.JFNKError as e:
+                    err = str(e)
+                    break
+                nn += st["newton_iterations"]
+                ng += st["gmres_iterations_total"]
+                napp += st["precond_applies"]
+                ncyc += st["inner_cycles"]
+                emean.append(st["inner_res_mean"] * st["precond_applies"])
+                emax = max(emax, st["inner_res_max"])
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            print(json.dumps({"study": "inner", "case": name, "arm": arm, "steps": args.steps,
+                              "steps_per_s": args.steps / el if err is None else None,
+                              "newton_per_step": nn / max(1, k + (err is None)),
+                              "gmres_per_newton": ng / max(1, nn), "vcycles_per_apply": ncyc / max(1, napp),
+                              "eta_inner_mean": sum(emean) / max(1, napp), "eta_inner_max": emax,
+                              "error": err}), flush=True)
+            del S
+            torch.cuda.empty_cache()
+
+
+def study_newton(args):
+    """--study newton: Newton convergence of the benchmark workload (problem 4
+    at --n^3, the benchmark's solver options) for each lambda of --lams
+    (default 1e-7, 1e-8, 1e-9, 1e-10): per step the Newton iterations, GMRES
+    iterations, ||F^|| at each iterate, ||R^-1 dX||_inf and the GMRES
+    residual estimate; per lambda the step rate and the largest scaled
+    difference of the final state from the first lambda's."""
+    import torch
+    from paper_1512_03662_gb300 import build as B
+    B.build()
+    import paper_1512_03662_gb300 as jf
+    prec = jf.FP64 if args.precision == "fp64" else jf.MIXED
+    lams = [float(x) for x in (args.lams or "1e-7,1e-8,1e-9,1e-10").split(",")]
+    first = None
+    for lam in lams:
+        wl = make_workload(args.n)
+        o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=prec, **{**OPT_OVERRIDES, "lam": lam})
+        S = jf.Solver.from_workload(wl, o)
+        X = torch.as_tensor(wl.X0, dtype=torch.float64, device="cuda")
+        dt = S.dt_from_cfl(X, wl.cfl_hydro)
+        nn = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            st = S.step(X, dt, NEWTON_TOL, ETA)
+            nn += st["newton_iterations"]
+            print(json.dumps({"study": "newton", "lam": lam, "step": k, "newton": st["newton_iterations"],
+                              "converged": st["converged"], "gmres": st["gmres_iterations"],
+                              "fhat": st["fhat_norm"], "dx_inf": st["dx_inf"], "gmres_res": st["gmres_res"]}),
+                  flush=True)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        _, R, _ = S.scaling(X)
+        if first is None:
+            first = X.clone()
+        print(json.dumps({"study": "newton_summary", "lam": lam, "n": args.n, "steps": args.steps,
+                          "steps_per_s": args.steps / el, "newton_per_step": nn / args.steps,
+                          "max_scaled_diff_vs_first_lambda": float(((X - first) / R).abs().max())}), flush=True)
+        del S
+        torch.cuda.empty_cache()
 
 
 def study_adjoint(args):
@@ -773,14 +978,21 @@ def main():
     ap.add_argument("--mg-nu2", type=int, default=None, help="post-smoothing sweeps")
     ap.add_argument("--eta", type=float, default=None,
                     help="GMRES relative tolerance (the paper's 1e-4 unless given)")
+    ap.add_argument("--lam", type=float, default=None,
+                    help="lambda of the perturbation size, Eq. pert_old (library default 1e-7)")
     ap.add_argument("--pc-freeze", type=int, default=None, choices=[0, 1],
                     help="1: preconditioner coefficients from X^n for the whole step")
-    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner", "adjoint", "machsweep"], default=None,
+    ap.add_argument("--study", choices=["tgv", "vortex", "params", "inner", "adjoint", "machsweep", "newton"],
+                    default=None,
                     help="tgv: the Taylor-Green iteration and decay study of Sect. 5.1.2; vortex: the "
                          "isentropic-vortex accuracy study of Sects. 3.7 and 5.1.1; params: the JFNK+PBP "
                          "parameter variants of Sect. 5.1.1 on the vortex; inner: V-cycle count and frozen "
                          "coefficients; adjoint: forward and backward time of the adjoint workload; "
-                         "machsweep: FP64 and mixed steps of the 3D vortex tube per Mach number (JSON lines)")
+                         "machsweep: FP64 and mixed steps of the 3D vortex tube per Mach number; newton: Newton "
+                         "convergence of the benchmark workload per lambda (JSON lines)")
+    ap.add_argument("--lams", default=None, help="lambdas of --study newton (default 1e-7,1e-8,1e-9,1e-10)")
+    ap.add_argument("--lam-arm", type=float, default=LAM_ARM,
+                    help="lambda of the extra mixed-precision arm of the benchmark line (0: none)")
     ap.add_argument("--machs", default=None,
                     help="Mach numbers of --study tgv (default 1e-1,...,1e-6) or machsweep (1e-2,1e-4,1e-6)")
     ap.add_argument("--decay", action="store_true", help="--study tgv: decay run to t = 20")
@@ -788,13 +1000,21 @@ def main():
                     help="cells per direction of --study tgv (default 64) or machsweep (128)")
     ap.add_argument("--cfl", type=float, default=None, help="--study machsweep: CFL_hydro instead of 1000")
     ap.add_argument("--ref-n", type=int, default=32,
-                    help="cells per direction of the oracle sample (--impl reference, cpu_baseline)")
+                    help="cells per direction of the oracle step of --impl reference")
+    ap.add_argument("--cpu-n", type=int, default=64,
+                    help="cells per direction of the oracle step of cpu_baseline")
+    ap.add_argument("--oracle-reps", type=int, default=3,
+                    help="cpu_baseline: oracle residual and Jv calls at full size, all threads")
+    ap.add_argument("--no-oracle-kernels", action="store_true",
+                    help="cpu_baseline without the full-size oracle residual and Jv timings")
+    ap.add_argument("--no-oracle-1thread", action="store_true",
+                    help="cpu_baseline without the single-thread full-size oracle timings")
     ap.add_argument("--sweep", action="store_true", help="--study tgv: GMRES iterations against CFL_hydro")
     args = ap.parse_args()
     if args.eta is not None:
         global ETA
         ETA = args.eta
-    for k in ("mg_cycles", "mg_nu1", "mg_nu2", "pc_freeze"):
+    for k in ("mg_cycles", "mg_nu1", "mg_nu2", "pc_freeze", "lam"):
         if getattr(args, k) is not None:
             OPT_OVERRIDES[k] = getattr(args, k)
             CLI_OPTS[k] = getattr(args, k)
@@ -812,6 +1032,9 @@ def main():
         return
     if args.study == "machsweep":
         study_machsweep(args)
+        return
+    if args.study == "newton":
+        study_newton(args)
         return
     if args.only:
         kernel_main(args)
@@ -834,6 +1057,10 @@ def main():
     stream = torch.cuda.Stream(device)
     wl = make_workload(args.n)
     peaks = load_peaks()
+    try:
+        probe = fp64_probe(device, stream)
+    except (OSError, RuntimeError) as e:
+        probe = {"error": str(e)}
 
     clocks = ClockSampler(local)
     barrier(ws)
@@ -845,6 +1072,7 @@ def main():
     barrier(ws)
     clk = clocks.stop()
     ms_mixed = max_over_ranks(ws, ms_mixed)
+    conv = {"mixed": convergence(st_mixed)}
 
     # the end-to-end arm right after the device arm, under the same conditions
     # (before the FP64 arm heats the GPU), with its own clock record
@@ -853,16 +1081,18 @@ def main():
         clocks_e2e = ClockSampler(local)
         barrier(ws)
         clocks_e2e.start()
-        ms_e2e, nbytes = e2e_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream)
+        ms_e2e, nbytes, st_e2e = e2e_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream)
         barrier(ws)
         clk_e2e = clocks_e2e.stop()
         ms_e2e = max_over_ranks(ws, ms_e2e)
+        conv["e2e"] = convergence(st_e2e)
         e2e = {"value": ws * args.steps / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "clocks": clk_e2e}
 
     fp64 = None
     if not args.no_fp64:
         S64, _, _, ms64, st64, X64 = run_arm(jf, wl, jf.FP64, args.steps, args.warmup, device, stream, True)
+        conv["fp64"] = convergence(st64)
         # the same steps in both precisions: max over unknowns of |X_mixed - X_fp64| / R(X_fp64)
         _, R64, _ = S64.scaling(X64)
         mixed_vs_fp64 = float(((X_mixed - X64) / R64).abs().max())
@@ -893,6 +1123,28 @@ def main():
             fp64["jv_gcell_s"] = njv64 * wl.ncell / (jv64 / 1e3) / 1e9
         del S64
 
+    lam_arm = None
+    if args.lam_arm > 0:
+        OPT_OVERRIDES["lam"], lam0 = args.lam_arm, OPT_OVERRIDES.get("lam")
+        clocks_l = ClockSampler(local)
+        clocks_l.start()
+        S_l, _, _, ms_l, st_l, X_l = run_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream, False)
+        clk_l = clocks_l.stop()
+        if lam0 is None:
+            del OPT_OVERRIDES["lam"]
+        else:
+            OPT_OVERRIDES["lam"] = lam0
+        conv["mixed_lam_arm"] = convergence(st_l)
+        _, R_l, _ = S_l.scaling(X_mixed)
+        ms_l = max_over_ranks(ws, ms_l)
+        nl = sum(s["newton_iterations"] for s in st_l)
+        lam_arm = {"lam": args.lam_arm, "steps_per_s": ws * args.steps / (ms_l / 1e3),
+                   "ms_per_step": ms_l / args.steps, "newton_per_step": nl / len(st_l),
+                   "gmres_per_newton": sum(s["gmres_iterations_total"] for s in st_l) / max(1, nl),
+                   "max_scaled_diff_vs_headline": float(((X_l - X_mixed) / R_l).abs().max()),
+                   "clocks": clk_l}
+        del S_l, X_l, R_l
+
     steps_per_s = ws * args.steps / (ms_mixed / 1e3)
     njv = sum(s["jv_evaluations"] for s in st_mixed)
     jv_ms = sum(s["jv_ms"] for s in st_mixed)
@@ -906,29 +1158,53 @@ def main():
     tinst = FP64_INST_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e12
     hbm_gbs = HBM_BYTES_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e9
     scale = wl.ncell / 128 ** 3
+    stale = kernel_source_hash() != KERNEL_COUNTS_HASH
+    if "tinst_s" in probe:
+        peak_tinst, peak_tflops = probe["tinst_s"], probe["tflops"]
+        peak_src = (f"measured: DFMA probe (libfp64probe.so, {probe['sms']} SMs x 8 blocks x 256 threads, "
+                    f"8 independent chains), best of {probe['launches']} launches, median SM clock "
+                    f"{probe['clocks'].get('sm_mhz')} MHz")
+    else:
+        peak_tinst, peak_tflops = FP64_PEAK_TINST, FP64_PEAK_TFLOPS
+        peak_src = "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz (probe failed)"
+    # the whole Jacobian-free product: FP64 instructions of its five kernels
+    # over their summed device time
+    jv_inst = sum(FP64_INST_PER_CELL[k] for k in JV_KERNELS) * wl.ncell * njv
+    jv_tinst = jv_inst / (jv_ms / 1e3) / 1e12 if jv_ms > 0 else None
     # The kernel is bound by the FP64 pipe, which issues one DADD, DMUL or DFMA
     # per lane slot whatever its flop count, so the roofline is stated in FP64
-    # instructions per second against the issue peak; the flop rate (DFMA = 2)
-    # is reported beside it.
-    roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": tinst, "peak": FP64_PEAK_TINST,
-                "unit": "T FP64 inst/s", "frac": tinst / FP64_PEAK_TINST,
-                "traffic": DRAM_BYTES_PER_CELL_128[name] * 128 ** 3 * scale,
+    # instructions per second against the measured issue rate; the flop rate
+    # (DFMA = 2) is reported beside it.
+    roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": tinst, "peak": peak_tinst,
+                "unit": "T FP64 inst/s", "frac": tinst / peak_tinst,
+                "traffic": None if stale else DRAM_BYTES_PER_CELL_128[name] * 128 ** 3 * scale,
                 "traffic_note": "ncu DRAM bytes of a 128^3 launch scaled by the cell ratio",
-                "peak_src": "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz",
+                "peak_src": peak_src, "counts_stale": stale, "counts_hash": KERNEL_COUNTS_HASH,
                 "fp64_inst_per_cell": FP64_INST_PER_CELL[name],
-                "achieved_tflops": achieved_tflops, "peak_tflops": FP64_PEAK_TFLOPS,
-                "frac_tflops": achieved_tflops / FP64_PEAK_TFLOPS,
+                "achieved_tflops": achieved_tflops, "peak_tflops": peak_tflops,
+                "frac_tflops": achieved_tflops / peak_tflops,
                 "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"],
-                "algorithmic_bytes_per_cell": HBM_BYTES_PER_CELL[name]}
+                "algorithmic_bytes_per_cell": HBM_BYTES_PER_CELL[name],
+                "jv_whole": {"fp64_inst_per_cell": sum(FP64_INST_PER_CELL[k] for k in JV_KERNELS),
+                             "achieved": jv_tinst, "frac": jv_tinst / peak_tinst if jv_tinst else None,
+                             "ms_per_product": jv_ms / max(1, njv)}}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_small = args.ref_n
-        s, threads = oracle_sample(n_small, 1)
-        v = (n_small / args.n) ** 3 / s
+        import torch as _t
+        oracle_sample(16, 1)                                  # first-call overheads of the oracle
+        s_step, threads, st_small = oracle_sample(args.cpu_n, 1, with_stats=True)
+        v = (args.cpu_n / args.n) ** 3 / s_step
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"one oracle implicit step at {n_small}^3 (same construction and dt), "
-                         f"time scaled by the cell ratio ({args.n}/{n_small})^3"}
+               "sample": f"one oracle implicit step at {args.cpu_n}^3 (same construction and dt, same solver "
+                         f"settings) took {s_step:.1f} s with {threads} threads; value = its rate x "
+                         f"({args.cpu_n}/{args.n})^3",
+               "step_small": {"n": args.cpu_n, "seconds": s_step, **st_small},
+               "host": cpu_info()}
+        if not args.no_oracle_kernels:
+            cpu["kernels_at_full_size"] = [oracle_kernels(wl, _t.get_num_threads(), args.oracle_reps)]
+            if not args.no_oracle_1thread:
+                cpu["kernels_at_full_size"].append(oracle_kernels(wl, 1, 1))
 
     if rank == 0:
         line = {"metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -939,17 +1215,23 @@ def main():
                                        f"dt {dt:.4g}",
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "state (670 MB/vector) larger than L2, no flush", "solver": solver_cfg},
+                "convergence": conv,
                 "jv_gcell_s": njv * wl.ncell / (jv_ms / 1e3) / 1e9 if jv_ms > 0 else None,
                 "newton_per_step": sum(s["newton_iterations"] for s in st_mixed) / len(st_mixed),
                 "gmres_per_newton": sum(s["gmres_iterations_total"] for s in st_mixed) /
                 max(1, sum(s["newton_iterations"] for s in st_mixed)),
-                "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "fp64": fp64, "lambda_arm": lam_arm, "roofline": roofline, "fp64_probe": probe,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk,
                 "jv_kernel_ms_per_launch": {JV_KERNELS[q]: kms[q] / max(1, njv) for q in range(5)},
                 "precond_ms_per_apply": sum(s["precond_ms"] for s in st_mixed) /
                 max(1, sum(s["precond_applies"] for s in st_mixed)),
                 "ortho_ms_per_iteration": sum(s["ortho_ms"] for s in st_mixed) / max(1, njv)}
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
+    # a rate is only claimed for steps that met the Newton tolerance
+    if any(c["newton_capped"] for c in conv.values()):
+        sys.stderr.write(f"bench: timed steps stopped without meeting the Newton tolerance: {conv}\n")
+        sys.exit(3)
 
 
 if __name__ == "__main__":

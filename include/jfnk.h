@@ -91,12 +91,22 @@ typedef struct { double K0; double exponent; } jfnk_conductivity;
  * pc_freeze = 1 takes the semi-implicit coefficients and transforms of the
  * preconditioner from X^n, the time level at which Sects. 3.3-3.4 write them,
  * for every Newton iteration of a step (only the scaling L, R follows the
- * iterate); 0 (default) rebuilds them at every Newton iterate. */
+ * iterate); 0 (default) rebuilds them at every Newton iterate.
+ * Inner tolerance (the eta' of Sect. 3.5): inner_tol = 0 (default) runs the
+ * fixed mg_cycles; inner_tol > 0 repeats V-cycles until the relative residual
+ * ||b - A x|| / ||b|| of the finest-level SI system is at most inner_tol, or
+ * inner_max_cycles cycles have run (the host reads the residual after every
+ * cycle).  GMRES keeps the preconditioned directions, so a cycle count that
+ * varies between applies leaves it valid (flexible GMRES).  inner_monitor =
+ * 1 measures that relative residual after every apply inside GMRES and
+ * reports it in the step statistics, at two extra reductions per apply. */
 typedef struct {
     double theta, lambda, alpha1, alpha2, eta, newton_tol;
     int pert, gmres_m, gmres_max_it, newton_min, newton_max;
     int precond, mg_cycles, mg_nu1, mg_nu2, precision, reorth, fixed_iterations;
     int pc_freeze;
+    double inner_tol;
+    int inner_max_cycles, inner_monitor;
 } jfnk_options;
 
 #define JFNK_MAX_NEWTON 64
@@ -121,6 +131,13 @@ typedef struct {
      * GMRES, in the order perturb, eos, face fluxes, momentum fluxes, assemble */
     double jv_kernel_ms[5];
     long long kernel_launches;              /* kernels launched during the call      */
+    /* with inner_monitor or inner_tol: the relative residual ||b - A x||/||b||
+     * of the finest-level SI system after each preconditioner apply inside
+     * GMRES (the inner accuracy eta' reached), mean and maximum over the
+     * applies, and the V-cycles run in all applies */
+    double inner_res_mean;
+    double inner_res_max;
+    long long inner_cycles;
 } jfnk_stats;
 
 typedef struct jfnk_handle jfnk_handle;
@@ -200,8 +217,10 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
 /* Vector-Jacobian product of the residual (the kernel of the step adjoint;
  * the paper has no adjoint): y = (dG/dX)^T w at X with G = U/dt - theta R_U,
  * i.e. the transpose of dF_U/dX of Eq. crank_nicholson.  Double vectors,
- * packed; wall slots of y are zero.  Hand-written reverse of the residual
- * kernels; atomic accumulation makes y reproducible to round-off only. */
+ * packed; wall slots of y are zero.  Needs an FP64 handle (JFNK_EINVAL on a
+ * mixed one, whose workspace holds no adjoint scratch).  Hand-written
+ * reverse of the residual kernels; atomic accumulation makes y reproducible
+ * to round-off only. */
 jfnk_status jfnk_vjp_residual(jfnk_handle* h, const double* X, double dt, const double* w, double* y);
 
 /* Adjoint of one implicit step (needs an FP64 handle).  Given the step's

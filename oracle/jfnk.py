@@ -16,8 +16,10 @@ package docstring for who may import this.
 * GMRES (Eq. forcing_term, Sect. 4.3 right preconditioning): start from 0,
   stop when the least-squares residual estimate is below eta ||F^||_2,
   restart length m, at most max_it iterations in total.  Classical
-  Gram-Schmidt (optionally a second pass), Givens rotations on the Hessenberg
-  matrix.  The preconditioned directions z_j = M^-1 v_j are kept so that the
+  Gram-Schmidt; reorth = 1 always adds a second pass, reorth = 2 adds it
+  only when the first pass shrank the vector below 1/sqrt(2) of its norm
+  (the selective criterion of Daniel, Gragg, Kaufman and Stewart, Math. Comp.
+  30 (1976) 772-795).  Givens rotations on the Hessenberg matrix.  The preconditioned directions z_j = M^-1 v_j are kept so that the
   correction is sum_j y_j z_j; for a fixed linear M this equals the paper's
   M^-1 (V y).
 * Newton (Eq. jacobian_system, nr_terminate): X^(0) = X^n, stop when
@@ -53,7 +55,7 @@ class Options:
     mg_cycles: int = 2              # V(mg_nu1, mg_nu2) cycles per preconditioner apply
     mg_nu1: int = 2
     mg_nu2: int = 2
-    reorth: int = 0                # 1: always a second Gram-Schmidt pass
+    reorth: int = 0                # 1: always a second Gram-Schmidt pass, 2: selective (DGKS)
     fixed_iterations: bool = False # run exactly gmres_max_it / newton_max iterations
     exact_inner: bool = False      # solve the SI system with a sparse direct solver
     pc_freeze: bool = False        # SI coefficients from X^n (Sects. 3.3-3.4 write them at level n)
@@ -123,6 +125,10 @@ class GmresStats:
     converged: bool = False
     res_history: List[float] = dataclasses.field(default_factory=list)
     beta0: float = 0.0
+    reorth_passes: int = 0
+
+
+DGKS_KAPPA = 1.0 / math.sqrt(2.0)   # second pass when ||w after|| < kappa ||w before||
 
 
 def gmres(apply_A: Callable[[torch.Tensor], torch.Tensor],
@@ -156,15 +162,18 @@ def gmres(apply_A: Callable[[torch.Tensor], torch.Tensor],
             z = apply_Minv(V[j])
             Z.append(z)
             w = apply_A(z)
+            wn0 = float(torch.linalg.vector_norm(w))
             h = torch.stack([torch.dot(V[i], w) for i in range(j + 1)])
             for i in range(j + 1):
                 w = w - h[i] * V[i]
-            if reorth:
+            hn = float(torch.linalg.vector_norm(w))
+            if reorth == 1 or (reorth == 2 and hn < DGKS_KAPPA * wn0):
                 h2 = torch.stack([torch.dot(V[i], w) for i in range(j + 1)])
                 for i in range(j + 1):
                     w = w - h2[i] * V[i]
                 h = h + h2
-            hn = float(torch.linalg.vector_norm(w))
+                hn = float(torch.linalg.vector_norm(w))
+                st.reorth_passes += 1
             H[:j + 1, j] = h
             H[j + 1, j] = hn
             # apply the previous rotations, then form the new one

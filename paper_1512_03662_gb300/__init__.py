@@ -54,7 +54,8 @@ class jfnk_options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("theta", "lambda_", "alpha1", "alpha2", "eta", "newton_tol")] + \
                [(n, ctypes.c_int) for n in ("pert", "gmres_m", "gmres_max_it", "newton_min", "newton_max",
                                              "precond", "mg_cycles", "mg_nu1", "mg_nu2", "precision", "reorth",
-                                             "fixed_iterations", "pc_freeze")]
+                                             "fixed_iterations", "pc_freeze")] + \
+               [("inner_tol", ctypes.c_double), ("inner_max_cycles", ctypes.c_int), ("inner_monitor", ctypes.c_int)]
 
 
 class jfnk_stats(ctypes.Structure):
@@ -64,7 +65,9 @@ class jfnk_stats(ctypes.Structure):
                 ("gmres_converged", ctypes.c_int * MAX_NEWTON), ("converged", ctypes.c_int),
                 ("jv_evaluations", ctypes.c_int), ("precond_applies", ctypes.c_int), ("jv_ms", ctypes.c_double),
                 ("precond_ms", ctypes.c_double), ("ortho_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
-                ("jv_kernel_ms", ctypes.c_double * 5), ("kernel_launches", ctypes.c_longlong)]
+                ("jv_kernel_ms", ctypes.c_double * 5), ("kernel_launches", ctypes.c_longlong),
+                ("inner_res_mean", ctypes.c_double), ("inner_res_max", ctypes.c_double),
+                ("inner_cycles", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         k = self.newton_iterations
@@ -75,7 +78,8 @@ class jfnk_stats(ctypes.Structure):
                 "jv_evaluations": self.jv_evaluations, "precond_applies": self.precond_applies,
                 "jv_ms": self.jv_ms, "precond_ms": self.precond_ms, "ortho_ms": self.ortho_ms,
                 "step_ms": self.step_ms, "jv_kernel_ms": list(self.jv_kernel_ms),
-                "kernel_launches": self.kernel_launches}
+                "kernel_launches": self.kernel_launches, "inner_res_mean": self.inner_res_mean,
+                "inner_res_max": self.inner_res_max, "inner_cycles": self.inner_cycles}
 
 
 _lib = None

@@ -16,6 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libjfnk.so")
 SOURCES = ["residual.cu", "krylov.cu", "precond.cu", "adjoint.cu", "engine.cu", "noalloc.cu"]
+# the FP64 throughput probe of the benchmark: a library of its own, not part of the solver's C ABI
+PROBE_SOURCE = "fp64_probe.cu"
+PROBE_LIB = os.path.join(BUILD, "libfp64probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -60,9 +63,12 @@ def build(verbose: bool = False, force: bool = False, extra=()) -> str:
             raise RuntimeError(f"nvcc failed on {cmd[2]}")
         return r
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    ps = os.path.join(CSRC, PROBE_SOURCE)
+    if force or not _newer(PROBE_LIB, [ps]):
+        jobs.append([cc, "-shared", ps, "-o", PROBE_LIB] + _flags(extra) + ["-lcudart"])
+    with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
+    if any(j[2] != ps for j in jobs) or not os.path.exists(LIB):
         run([cc, "-shared", "-o", LIB] + objs + ARCH + ["-lcudart"])
     return LIB
 

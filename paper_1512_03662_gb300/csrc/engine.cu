@@ -30,6 +30,7 @@ struct jfnk_handle {
     char* ws;
     cudaStream_t stream;
     int device;        // device current at jfnk_bind (-1: never bound)
+    long long inner_cycles;   // V-cycles run by preconditioner applies (host count)
     double* hpin;      // pinned host scalars
     std::string err;
     int profiling;
@@ -110,14 +111,19 @@ size_t plan(jfnk_handle* h, char* base) {
     h->y = (double*)take(m * 8);
     h->vscale = (double*)take((m + 1) * 8);
     h->hc2 = (double*)take((m + 1) * 8);
-    h->adj = (double*)take(vjp_scratch_doubles(h->G) * 8);
-    h->Xb = (double*)take(nv * 8);
-    h->rub = (double*)take(nd * nc * 8);
-    h->reb = (double*)take(nc * 8);
-    h->rpb = (double*)take(nc * 8);
-    h->b64 = (double*)take(nv * 8);
-    h->lam = (double*)take(nv * 8);
-    h->w64 = (double*)take(nv * 8);
+    // the adjoint (jfnk_vjp, jfnk_vjp_residual) runs on FP64 handles only:
+    // mixed handles reserve none of its scratch
+    h->adj = h->Xb = h->rub = h->reb = h->rpb = h->b64 = h->lam = h->w64 = nullptr;
+    if (!h->mixed) {
+        h->adj = (double*)take(vjp_scratch_doubles(h->G) * 8);
+        h->Xb = (double*)take(nv * 8);
+        h->rub = (double*)take(nd * nc * 8);
+        h->reb = (double*)take(nc * 8);
+        h->rpb = (double*)take(nc * 8);
+        h->b64 = (double*)take(nv * 8);
+        h->lam = (double*)take(nv * 8);
+        h->w64 = (double*)take(nv * 8);
+    }
     h->jvP = (double*)take(nv * 8);
     h->jvQ = (double*)take(nv * 8);
     h->jvC = (double*)take(nv * 8);
@@ -266,7 +272,32 @@ void precond(jfnk_handle* h, const double* X, double dt, const T* v, int vslot, 
     (void)X;
     launch_precond_in<T>(h->G, (const T*)h->C, v, h->vscale, vslot, h->nf, (T*)h->rp, (T*)h->re, (T*)h->ru,
                          h->levels[0], s, h->opt.mg_nu1 > 0 ? 0 : 1);
-    for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<T>(h, 0, 0, c == 0);
+    MGLevel& L0 = h->levels[0];
+    const long long n0 = (long long)h->nf * L0.ncell;
+    const bool adaptive = h->opt.inner_tol > 0.0;
+    if (adaptive || h->opt.inner_monitor) {
+        launch_norm2_partials<T>((const T*)L0.rhs, n0, h->partials, s);
+        launch_finalize(h->partials, kRedBlocks, h->scal, kSlotInnerB, 0, s);
+    }
+    auto inner_residual = [&]() {
+        launch_mg_residual<T>(h->G, h->nf, L0, s);
+        launch_norm2_partials<T>((const T*)L0.r, n0, h->partials, s);
+        launch_finalize(h->partials, kRedBlocks, h->scal, kSlotInnerR, 0, s);
+    };
+    if (adaptive) {
+        // cycle until ||b - A x|| <= inner_tol ||b|| (a sync per cycle)
+        for (int c = 0; c < h->opt.inner_max_cycles; ++c) {
+            vcycle<T>(h, 0, 0, c == 0);
+            ++h->inner_cycles;
+            inner_residual();
+            if (sync_read(h) != JFNK_OK) break;       // the error resurfaces at the caller's next sync
+            if (!(h->hpin[kSlotInnerR] > h->opt.inner_tol * h->hpin[kSlotInnerB])) break;
+        }
+    } else {
+        for (int c = 0; c < h->opt.mg_cycles; ++c) vcycle<T>(h, 0, 0, c == 0);
+        h->inner_cycles += h->opt.mg_cycles;
+        if (h->opt.inner_monitor) inner_residual();
+    }
     const int np = launch_precond_out<T>(h->G, (const T*)h->C, dt, h->nf, (const T*)h->rp, (const T*)h->re,
                                          (const T*)h->ru, h->levels[0], z, h->partials, s);
     launch_finalize(h->partials, np, h->scal, kSlotZnorm, 0, s);
@@ -337,6 +368,8 @@ struct SolveOut {
     int jv = 0, pc = 0;
     double jv_ms = 0, pc_ms = 0, or_ms = 0;
     double kms[5] = {0, 0, 0, 0, 0};
+    double inner_sum = 0, inner_max = 0;
+    int inner_n = 0;
 };
 
 // GMRES on J^ M^-1, RHS in V[0] (unnormalised), solution accumulated in dxh.
@@ -398,6 +431,13 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
                 so.or_ms += Timer::ms(h, 8);
                 for (int q = 0; q < 5; ++q) so.kms[q] += ev_ms(h, q, q + 1);
                 so.jv_ms += ev_ms(h, 0, 5);
+            }
+            if ((h->opt.inner_monitor || h->opt.inner_tol > 0.0) && h->nf > 0) {
+                const double b = h->hpin[kSlotInnerB];
+                const double ratio = b > 0.0 ? h->hpin[kSlotInnerR] / b : 0.0;
+                so.inner_sum += ratio;
+                so.inner_max = std::max(so.inner_max, ratio);
+                so.inner_n++;
             }
             so.jv++;
             so.pc++;
@@ -543,6 +583,13 @@ jfnk_status gmres_adj(jfnk_handle* h, const double* X, double dt, double eta, So
             launch_set_subdiag(h->scal, hcol, j, h->vscale, s);
             launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
             if ((st = sync_read(h)) != JFNK_OK) return st;
+            if ((h->opt.inner_monitor || h->opt.inner_tol > 0.0) && h->nf > 0) {
+                const double b = h->hpin[kSlotInnerB];
+                const double ratio = b > 0.0 ? h->hpin[kSlotInnerR] / b : 0.0;
+                so.inner_sum += ratio;
+                so.inner_max = std::max(so.inner_max, ratio);
+                so.inner_n++;
+            }
             so.jv++;
             so.pc++;
             total++;
@@ -581,6 +628,8 @@ jfnk_status validate_options(jfnk_handle* h, const jfnk_options* o) {
     if (o->mg_cycles < 1 || o->mg_nu1 < 0 || o->mg_nu2 < 0) return fail(h, JFNK_EINVAL, "bad multigrid cycle counts");
     if (o->pc_freeze != 0 && o->pc_freeze != 1) return fail(h, JFNK_EINVAL, "pc_freeze must be 0 or 1");
     if (!(o->lambda > 0.0)) return fail(h, JFNK_EINVAL, "lambda must be positive");
+    if (!(o->inner_tol >= 0.0) || o->inner_max_cycles < 1 || (o->inner_monitor != 0 && o->inner_monitor != 1))
+        return fail(h, JFNK_EINVAL, "bad inner tolerance options");
     if (o->pert != JFNK_PERT_OLD && o->pert != JFNK_PERT_NEW) return fail(h, JFNK_EINVAL, "unknown perturbation rule");
     return JFNK_OK;
 }
@@ -617,6 +666,9 @@ void jfnk_default_options(jfnk_options* o) {
     o->reorth = 0;
     o->fixed_iterations = 0;
     o->pc_freeze = 0;
+    o->inner_tol = 0.0;
+    o->inner_max_cycles = 50;
+    o->inner_monitor = 0;
 }
 
 jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_gravity* gravity,
@@ -628,6 +680,7 @@ jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_eos* eos, const jfnk_g
     h->hpin = nullptr;
     h->stream = 0;
     h->device = -1;
+    h->inner_cycles = 0;
     h->profiling = 0;
     for (auto& e : h->ev) e = nullptr;
     if (opt) h->opt = *opt;
@@ -780,6 +833,7 @@ jfnk_status jfnk_linear_solve(jfnk_handle* h, const double* X, const double* Xn,
     if (!X || !Xn || !dxhat || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_linear_solve");
     eval<kModeBn, double>(h, Xn, dt, h->bn, (double*)nullptr);
     SolveOut so;
+    h->inner_cycles = 0;
     st = h->mixed ? newton_solve<float>(h, X, dt, h->opt.eta, so, true)
                   : newton_solve<double>(h, X, dt, h->opt.eta, so, true);
     if (st < 0) return st;
@@ -795,6 +849,9 @@ jfnk_status jfnk_linear_solve(jfnk_handle* h, const double* X, const double* Xn,
         stats->fhat_norm[0] = so.beta0;
         stats->jv_evaluations = so.jv;
         stats->precond_applies = so.pc;
+        stats->inner_res_mean = so.inner_n > 0 ? so.inner_sum / so.inner_n : 0.0;
+        stats->inner_res_max = so.inner_max;
+        stats->inner_cycles = h->inner_cycles;
     }
     return so.converged ? JFNK_OK : JFNK_ENOCONV_GMRES;
 }
@@ -811,6 +868,9 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
     memset(S, 0, sizeof *S);
     if (h->profiling) cudaEventRecord(h->ev[10], h->stream);
     const long long launches0 = g_launch_count;
+    h->inner_cycles = 0;
+    double inner_sum = 0.0;
+    int inner_n = 0;
     eval<kModeBn, double>(h, X, dt, h->bn, (double*)nullptr);      // X holds X^n here
     bool gmres_fail = false;
     for (int k = 0; k < h->opt.newton_max; ++k) {
@@ -836,6 +896,9 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
         S->precond_ms += so.pc_ms;
         S->ortho_ms += so.or_ms;
         for (int q = 0; q < 5; ++q) S->jv_kernel_ms[q] += so.kms[q];
+        inner_sum += so.inner_sum;
+        inner_n += so.inner_n;
+        S->inner_res_max = std::max(S->inner_res_max, so.inner_max);
         if (!so.converged) gmres_fail = true;
         if (!std::isfinite(dinf)) return fail(h, JFNK_ENONFINITE, "non-finite Newton correction");
         if (!h->opt.fixed_iterations && k + 1 >= h->opt.newton_min && dinf < ntol) {
@@ -849,6 +912,8 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
         S->step_ms = Timer::ms(h, 10);
     }
     S->kernel_launches = g_launch_count - launches0;
+    S->inner_res_mean = inner_n > 0 ? inner_sum / inner_n : 0.0;
+    S->inner_cycles = h->inner_cycles;
     if (!S->converged && !h->opt.fixed_iterations) return JFNK_ENOCONV_NEWTON;
     (void)gmres_fail;
     return JFNK_OK;
@@ -916,6 +981,7 @@ jfnk_status jfnk_vjp_residual(jfnk_handle* h, const double* X, double dt, const 
     jfnk_status st = check_bound(h);
     if (st) return st;
     if (!X || !w || !y || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_vjp_residual");
+    if (h->mixed) return fail(h, JFNK_EINVAL, "jfnk_vjp_residual needs an FP64 handle");
     vjp_apply(h, X, w, 1.0 / dt, -h->opt.theta, y);
     CUDA_TRY(h, cudaGetLastError());
     return JFNK_OK;

@@ -1,0 +1,46 @@
+// FP64 throughput probe: the measured peak that the FP64-bound stencil
+// kernels are compared against.
+//
+// Every thread runs eight independent chains of fused multiply-adds
+// x <- x * a + b (one DFMA instruction, two flops each), so the FP64 pipe
+// always has independent work to issue and the measured rate is its issue
+// limit.  With 0 < a < 1 and b = 1 - a every chain converges to 1.0 and
+// stays a normal number.  Each thread writes the sum of its chains so that
+// no chain is dead code.  This is not part of the solver library: bench.py
+// loads it on its own to time the probe with CUDA events.
+#include <cuda_runtime.h>
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_dfma_probe(double* out, int iters, double a, double b) {
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+// DFMA instructions one launch executes per thread.
+long long fp64_probe_fma_per_thread(int iters) { return (long long)iters * kChains; }
+
+// Queue one probe launch of `blocks` x 256 threads on `stream`; out holds
+// blocks * 256 doubles.  Returns the cudaError_t of the launch.
+int fp64_probe_launch(double* out, int blocks, int iters, double a, void* stream) {
+    if (!out || blocks <= 0 || iters <= 0 || !(a > 0.0 && a < 1.0)) return (int)cudaErrorInvalidValue;
+    k_dfma_probe<<<blocks, 256, 0, (cudaStream_t)stream>>>(out, iters, a, 1.0 - a);
+    return (int)cudaGetLastError();
+}
+
+}  // extern "C"

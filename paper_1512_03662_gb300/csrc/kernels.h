@@ -24,6 +24,8 @@ enum {
     kSlotTmp = 7,
     kSlotBeta0 = 8,
     kSlotInvDelta = 9,   // 1/delta of the current Jv (one division, not one per thread)
+    kSlotInnerB = 10,    // ||b||_2 of the finest-level SI system of the current preconditioner apply
+    kSlotInnerR = 11,    // ||b - A x||_2 after its V-cycles
     kNumSlots = 16
 };
 
@@ -139,6 +141,8 @@ void launch_smooth(const Grid& G, int nf, MGLevel& Lv, int colour, cudaStream_t 
 // colour-0 cells only
 template <typename T>
 void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr = 0, int red_only = 0);
+template <typename T>
+void launch_mg_residual(const Grid& G, int nf, MGLevel& F, cudaStream_t s);
 template <typename T>
 void launch_prolong(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s);
 template <typename T>

@@ -639,6 +639,17 @@ void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t
 template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 
+// r = rhs - A x on every cell of level F (the inner-solve residual that the
+// preconditioner's accuracy monitor and its tolerance-driven cycling read)
+template <typename T>
+void launch_mg_residual(const Grid& G, int nf, MGLevel& F, cudaStream_t s) {
+    CellLaunch fl = cell_launch(F.n);
+    MG_DISPATCH(k_residual_mg, fl.grid, fl.block, lvl(F), (const T*)F.M, (const T*)F.K, (const T*)F.x,
+                (const T*)F.rhs, (T*)F.r, 0, 0, 0);
+}
+template void launch_mg_residual<double>(const Grid&, int, MGLevel&, cudaStream_t);
+template void launch_mg_residual<float>(const Grid&, int, MGLevel&, cudaStream_t);
+
 // Cell-centred linear prolongation x_f += P x_c for one coarse cell: load
 // the coarse neighbourhood once (3 values along each coarsened direction)
 // and update the cell's 2^k children.  A child at offset

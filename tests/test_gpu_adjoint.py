@@ -191,3 +191,14 @@ def test_vjp_rejects_mixed_precision_handles(jf):
     with pytest.raises(jf.JFNKError) as e:
         S.vjp(X, X, dt, X)
     assert e.value.status == jf.JFNK_EINVAL
+
+
+def test_vjp_residual_rejects_mixed_precision_handles(jf):
+    """Mixed handles reserve no adjoint scratch, so the transposed product
+    is refused there too."""
+    wl, P, dt = _small(8)
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=wl.precond, precision=jf.MIXED))
+    X = _dev(wl.X0)
+    with pytest.raises(jf.JFNKError) as e:
+        S.vjp_residual(X, dt, X)
+    assert e.value.status == jf.JFNK_EINVAL

@@ -55,8 +55,9 @@ def test_full_size_handles_plan_on_the_host(jf, cid):
         L.jfnk_destroy(h)
     assert 0 < sizes[jf.MIXED] < sizes[jf.FP64]
     if cid == 4:
-        # 256^3: about 40 GB mixed, 64 GB FP64, both far inside the 288 GB of HBM
-        assert sizes[jf.MIXED] < 48e9 and sizes[jf.FP64] < 72e9
+        # 256^3: about 34 GB mixed (no adjoint scratch: the adjoint runs on
+        # FP64 handles only), 64 GB FP64, both far inside the 288 GB of HBM
+        assert sizes[jf.MIXED] < 36e9 and sizes[jf.FP64] < 72e9
 
 
 def test_workspace_grows_with_the_krylov_basis(jf):

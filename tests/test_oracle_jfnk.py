@@ -357,3 +357,48 @@ def test_si_step_reduces_to_forward_euler():
         errs.append(float(((X1 - X) / dt - target).norm() / target.norm()))
     assert errs[1] < 3e-3, errs
     assert errs[0] / errs[1] > 5.0, errs            # at least first order in dt
+
+
+def _krylov_basis_loss(reorth, n=60, m=30):
+    """Orthogonality of the GMRES basis on the diagonal operator with
+    eigenvalues 2^0 ... 2^(n-1) and b = 1: max |V^T V - I| over the m basis
+    vectors (with no preconditioner GMRES applies the operator to the basis
+    vectors themselves, so they are captured there)."""
+    d = 2.0 ** torch.arange(n, dtype=torch.float64)
+    b = torch.ones(n, dtype=torch.float64)
+    seen = []
+
+    def A(v):
+        seen.append(v.clone())
+        return d * v
+    _, st = J.gmres(A, lambda v: v, b, 1e-30, m, m, reorth=reorth, fixed=True)
+    V = torch.stack(seen)
+    return float((V @ V.T - torch.eye(len(seen), dtype=torch.float64)).abs().max()), st
+
+
+def test_selective_reorthogonalisation_restores_an_orthogonal_basis():
+    """Classical Gram-Schmidt loses orthogonality on an ill-conditioned
+    Krylov sequence (30 vectors; eigenvalues spread over 2^0 ... 2^59: the
+    basis drifts to 2.5e-7 from orthogonal); the selective second pass
+    (Daniel, Gragg, Kaufman and Stewart 1976: re-project when the first pass
+    shrank the vector below 1/sqrt(2) of its norm) keeps it at round-off,
+    with fewer passes than the unconditional second pass."""
+    loss0, st0 = _krylov_basis_loss(0)
+    loss2, st2 = _krylov_basis_loss(2)
+    loss1, st1 = _krylov_basis_loss(1)
+    assert loss0 > 1e-8, loss0
+    assert loss2 < 1e-14 and loss1 < 1e-14, (loss2, loss1)
+    assert st0.reorth_passes == 0 and st1.reorth_passes == 30
+    assert 0 < st2.reorth_passes < 30, st2.reorth_passes
+
+
+def test_selective_reorthogonalisation_keeps_the_gmres_solution():
+    """On a well-conditioned problem the criterion never fires and the
+    solution is that of plain GMRES; with it the restarted solve of the 8x8
+    Newton system still matches the dense solve."""
+    d = torch.linspace(1.0, 3.0, 50, dtype=torch.float64)
+    b = torch.ones(50, dtype=torch.float64)
+    x0, s0 = J.gmres(lambda v: d * v, lambda v: v, b, 1e-12, 10, 100, reorth=0)
+    x2, s2 = J.gmres(lambda v: d * v, lambda v: v, b, 1e-12, 10, 100, reorth=2)
+    assert torch.allclose(x2, b / d, rtol=1e-10)
+    assert float((x2 - x0).abs().max()) < 1e-13
