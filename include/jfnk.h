@@ -85,7 +85,11 @@ typedef struct { double K0; double exponent; } jfnk_conductivity;
  * restart length, gmres_max_it the total iteration cap per linear solve,
  * newton_min = 2 forces the second iteration of Sect. 4.1.  mg_cycles V-cycles
  * (default 2) with mg_nu1 / mg_nu2 (default 2 / 2) red-black Gauss-Seidel
- * sweeps solve the semi-implicit system.  reorth = 1 adds a second classical Gram-Schmidt pass.
+ * sweeps solve the semi-implicit system.  reorth = 1 adds a second classical
+ * Gram-Schmidt pass to every GMRES iteration; reorth = 2 adds it only when
+ * the first pass shrank the new Krylov vector below 1/sqrt(2) of its norm
+ * (Daniel, Gragg, Kaufman and Stewart 1976; one extra host read per
+ * iteration).
  * fixed_iterations = 1 runs exactly gmres_max_it iterations per linear solve
  * and newton_max Newton iterations (reproducible iteration counts).
  * pc_freeze = 1 takes the semi-implicit coefficients and transforms of the
@@ -138,6 +142,7 @@ typedef struct {
     double inner_res_mean;
     double inner_res_max;
     long long inner_cycles;
+    long long reorth_passes;                /* second Gram-Schmidt passes run         */
 } jfnk_stats;
 
 typedef struct jfnk_handle jfnk_handle;

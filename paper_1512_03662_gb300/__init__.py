@@ -67,7 +67,7 @@ class jfnk_stats(ctypes.Structure):
                 ("precond_ms", ctypes.c_double), ("ortho_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
                 ("jv_kernel_ms", ctypes.c_double * 5), ("kernel_launches", ctypes.c_longlong),
                 ("inner_res_mean", ctypes.c_double), ("inner_res_max", ctypes.c_double),
-                ("inner_cycles", ctypes.c_longlong)]
+                ("inner_cycles", ctypes.c_longlong), ("reorth_passes", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         k = self.newton_iterations
@@ -79,7 +79,8 @@ class jfnk_stats(ctypes.Structure):
                 "jv_ms": self.jv_ms, "precond_ms": self.precond_ms, "ortho_ms": self.ortho_ms,
                 "step_ms": self.step_ms, "jv_kernel_ms": list(self.jv_kernel_ms),
                 "kernel_launches": self.kernel_launches, "inner_res_mean": self.inner_res_mean,
-                "inner_res_max": self.inner_res_max, "inner_cycles": self.inner_cycles}
+                "inner_res_max": self.inner_res_max, "inner_cycles": self.inner_cycles,
+                "reorth_passes": self.reorth_passes}
 
 
 _lib = None

@@ -64,7 +64,7 @@ def build(verbose: bool = False, force: bool = False, extra=()) -> str:
         return r
 
     ps = os.path.join(CSRC, PROBE_SOURCE)
-    if force or not _newer(PROBE_LIB, [ps]):
+    if force or not _newer(PROBE_LIB, [ps] + headers):
         jobs.append([cc, "-shared", ps, "-o", PROBE_LIB] + _flags(extra) + ["-lcudart"])
     with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))

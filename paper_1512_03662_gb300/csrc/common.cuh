@@ -20,6 +20,7 @@ struct Grid {
     int bc[3];                       // 0 periodic, 1 wall
     double gamma, gm1;
     double g[3];
+    double hg[3];                    // g / 2 (the face density enters as the cell sum)
     double K0, chi_exp;
     int energy_form;                 // 0 internal e, 1 total eps_t
     double theta;
@@ -38,6 +39,7 @@ inline void set_grid_flags(Grid& G) {
     G.chi3 = G.chi_exp == 3.0;
     G.igm1 = 1.0 / G.gm1;
     G.igamma = 1.0 / G.gamma;
+    for (int d = 0; d < 3; ++d) G.hg[d] = 0.5 * G.g[d];
 }
 
 struct Idx3 { int i[3]; };
@@ -189,14 +191,47 @@ __device__ __forceinline__ Upw upwind_parts(double q_near, double q_far, double 
     return u;
 }
 
-// r[i] = 1/d[i], i < K, with one division: Montgomery's simultaneous
+// x / 2, exactly: for a normal x whose biased exponent exceeds 1 (the
+// common case) an exponent decrement of the high word on the integer pipe,
+// with no FP64 instruction; zero, subnormal, infinite and NaN values take
+// the FP64 product, in a branch that only warps holding such a value enter.
+__device__ __forceinline__ double half_exact(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    double r = __hiloint2double(hi - 0x00100000, __double2loint(x));
+    const bool slow = (e - 2u) > 0x7fcu;          // e < 2 or e == 0x7ff
+    if (__any_sync(__activemask(), slow)) {
+        if (slow) r = 0.5 * x;
+    }
+    return r;
+}
+
+// 1/d by Newton-Raphson iteration for the reciprocal (Markstein, IBM J.
+// Res. Dev. 34 (1990) 111-119): from the hardware approximation r0
+// (rcp.approx.ftz.f64, MUFU pipe) each step r <- r + r (1 - d r) squares the
+// relative error, two fused multiply-adds per step.  Two steps leave the
+// rounding of the last step, within one ulp of the correctly rounded 1/d,
+// in four FP64 instructions instead of an IEEE division sequence.  Valid
+// for normal d whose reciprocal is normal (the approximation flushes
+// subnormals); callers guarantee the range.
+__device__ __forceinline__ double recip_nr(double d) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
+// r[i] = 1/d[i], i < K, with one reciprocal: Montgomery's simultaneous
 // inversion (P. L. Montgomery, Math. Comp. 48 (1987) 243-264):
-// prefix products p_i = d_0 ... d_i, one reciprocal 1/p_{K-1}, then going
-// down r_i = p_{i-1} / p_i and 1/p_{i-1} = d_i / p_i.  It costs 3(K-1)
-// multiplications instead of K-1 divisions; each result carries at most 3K
-// roundings instead of one.  The prefix products stay in the normal range
-// when every |d_i| lies in [2^-R, 2^R), R = 1000/K (exponent test on the high
-// word, integer pipe); otherwise the thread divides K times.
+// prefix products p_i = d_0 ... d_i, one reciprocal 1/p_{K-1} (recip_nr),
+// then going down r_i = p_{i-1} / p_i and 1/p_{i-1} = d_i / p_i.  It costs
+// 3(K-1) multiplications instead of K-1 divisions; each result carries at
+// most 3K + 1 roundings instead of one.  The prefix products stay in the
+// normal range when every |d_i| lies in [2^-R, 2^R), R = 1000/K (exponent
+// test on the high word, integer pipe); otherwise the thread divides K
+// times.
 template <int K>
 __device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K]) {
     constexpr unsigned R = 1000u / K;
@@ -211,7 +246,7 @@ __device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K]) 
         p[0] = d[0];
 #pragma unroll
         for (int i = 1; i < K; ++i) p[i] = p[i - 1] * d[i];
-        double inv = 1.0 / p[K - 1];
+        double inv = recip_nr(p[K - 1]);
 #pragma unroll
         for (int i = K - 1; i > 0; --i) {
             r[i] = inv * p[i - 1];

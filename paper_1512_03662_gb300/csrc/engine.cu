@@ -370,7 +370,45 @@ struct SolveOut {
     double kms[5] = {0, 0, 0, 0, 0};
     double inner_sum = 0, inner_max = 0;
     int inner_n = 0;
+    int reorth = 0;      // second Gram-Schmidt passes
 };
+
+// Classical Gram-Schmidt of the new Arnoldi vector Vn = V[j+1] against
+// V[0..j]: coefficients into hcol, partial sums of |Vn|^2 after the
+// projection left in h->partials (the count is returned in nb).  reorth = 1
+// adds a second pass always; reorth = 2 adds it only when the first pass
+// shrank the vector below kDgksKappa of its norm (the selective criterion of
+// Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30 (1976) 772-795), which
+// the host decides from two norms read back; `passes` counts second passes.
+constexpr double kDgksKappa = 0.70710678118654752440;   // 1/sqrt(2)
+
+template <typename T>
+jfnk_status gram_schmidt(jfnk_handle* h, const T* V, T* Vn, int j, double* hcol, int& nb, int& passes) {
+    cudaStream_t s = h->stream;
+    const long long n = h->nvec, ld = h->ldv;
+    if (h->opt.reorth == 2) {
+        launch_norm2_partials<T>(Vn, n, h->partials, s);
+        launch_finalize(h->partials, kRedBlocks, h->scal, kSlotWnorm0, 0, s);
+    }
+    nb = launch_multidot<T>(V, ld, j + 1, Vn, n, h->partials, s);
+    launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, hcol, 0, s);
+    nb = launch_axpy_norm<T>(Vn, V, ld, j + 1, hcol, h->vscale, n, h->partials, s);
+    bool second = h->opt.reorth == 1;
+    if (h->opt.reorth == 2) {
+        launch_finalize(h->partials, nb, h->scal, kSlotTmp, 0, s);
+        jfnk_status st = sync_read(h);
+        if (st != JFNK_OK) return st;
+        second = h->hpin[kSlotTmp] < kDgksKappa * h->hpin[kSlotWnorm0];
+    }
+    if (second) {
+        nb = launch_multidot<T>(V, ld, j + 1, Vn, n, h->partials, s);
+        launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, h->hc2, 0, s);
+        nb = launch_axpy_norm<T>(Vn, V, ld, j + 1, h->hc2, h->vscale, n, h->partials, s);
+        launch_add_col(hcol, h->hc2, j + 1, s);
+        ++passes;
+    }
+    return JFNK_OK;
+}
 
 // GMRES on J^ M^-1, RHS in V[0] (unnormalised), solution accumulated in dxh.
 template <typename T>
@@ -408,18 +446,9 @@ jfnk_status gmres(jfnk_handle* h, const double* X, double dt, double eta, SolveO
             {
                 Timer t(h, 8);
                 double* hcol = h->H + (long long)j * ldh;
-                const long long ld = h->ldv;
-                int nb = launch_multidot<T>(Vcol<T>(h, 0), ld, j + 1, Vcol<T>(h, j + 1), n, h->partials, s);
-                launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, hcol, 0, s);
-                nb = launch_axpy_norm<T>(Vcol<T>(h, j + 1), Vcol<T>(h, 0), ld, j + 1, hcol, h->vscale, n, h->partials,
-                                         s);
-                if (h->opt.reorth) {
-                    nb = launch_multidot<T>(Vcol<T>(h, 0), ld, j + 1, Vcol<T>(h, j + 1), n, h->partials, s);
-                    launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, h->hc2, 0, s);
-                    nb = launch_axpy_norm<T>(Vcol<T>(h, j + 1), Vcol<T>(h, 0), ld, j + 1, h->hc2, h->vscale, n,
-                                             h->partials, s);
-                    launch_add_col(hcol, h->hc2, j + 1, s);
-                }
+                int nb = 0;
+                if ((st = gram_schmidt<T>(h, Vcol<T>(h, 0), Vcol<T>(h, j + 1), j, hcol, nb, so.reorth)) != JFNK_OK)
+                    return st;
                 launch_finalize(h->partials, nb, h->scal, kSlotTmp, 0, s);
                 launch_set_subdiag(h->scal, hcol, j, h->vscale, s, kSlotInvDelta);
                 launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
@@ -476,7 +505,7 @@ template <typename T>
 void linearize(jfnk_handle* h, const double* X, double dt, bool full_setup) {
     scaling(h, X);
     eval<kModeNewton, T>(h, X, dt, h->G0, Vcol<T>(h, 0));
-    launch_jv_coeffs(h->Linv, h->G0, dt, h->opt.theta, h->jvP, h->jvQ, h->jvC, h->nvec, h->stream);
+    launch_jv_coeffs(h->Linv, h->G0, dt, h->opt.theta, h->jvP, h->jvQ, h->jvC, h->nvec, 2 * h->nc, h->stream);
     if (full_setup) {
         si_setup(h, X, dt);
     } else if (h->nf > 0) {
@@ -570,26 +599,12 @@ jfnk_status gmres_adj(jfnk_handle* h, const double* X, double dt, double eta, So
             precond_T(h, dt, h->w64, Zj);
             jT_apply(h, X, dt, Zj, Vn);
             double* hcol = h->H + (long long)j * ldh;
-            int nb = launch_multidot<double>(V, ld, j + 1, Vn, n, h->partials, s);
-            launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, hcol, 0, s);
-            nb = launch_axpy_norm<double>(Vn, V, ld, j + 1, hcol, h->vscale, n, h->partials, s);
-            if (h->opt.reorth) {
-                nb = launch_multidot<double>(V, ld, j + 1, Vn, n, h->partials, s);
-                launch_multidot_finalize(h->partials, nb, j + 1, h->vscale, h->hc2, 0, s);
-                nb = launch_axpy_norm<double>(Vn, V, ld, j + 1, h->hc2, h->vscale, n, h->partials, s);
-                launch_add_col(hcol, h->hc2, j + 1, s);
-            }
+            int nb = 0;
+            if ((st = gram_schmidt<double>(h, V, Vn, j, hcol, nb, so.reorth)) != JFNK_OK) return st;
             launch_finalize(h->partials, nb, h->scal, kSlotTmp, 0, s);
             launch_set_subdiag(h->scal, hcol, j, h->vscale, s);
             launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->scal, s);
             if ((st = sync_read(h)) != JFNK_OK) return st;
-            if ((h->opt.inner_monitor || h->opt.inner_tol > 0.0) && h->nf > 0) {
-                const double b = h->hpin[kSlotInnerB];
-                const double ratio = b > 0.0 ? h->hpin[kSlotInnerR] / b : 0.0;
-                so.inner_sum += ratio;
-                so.inner_max = std::max(so.inner_max, ratio);
-                so.inner_n++;
-            }
             so.jv++;
             so.pc++;
             total++;
@@ -627,6 +642,7 @@ jfnk_status validate_options(jfnk_handle* h, const jfnk_options* o) {
     if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return fail(h, JFNK_EINVAL, "unknown precision");
     if (o->mg_cycles < 1 || o->mg_nu1 < 0 || o->mg_nu2 < 0) return fail(h, JFNK_EINVAL, "bad multigrid cycle counts");
     if (o->pc_freeze != 0 && o->pc_freeze != 1) return fail(h, JFNK_EINVAL, "pc_freeze must be 0 or 1");
+    if (o->reorth < 0 || o->reorth > 2) return fail(h, JFNK_EINVAL, "reorth must be 0, 1 or 2");
     if (!(o->lambda > 0.0)) return fail(h, JFNK_EINVAL, "lambda must be positive");
     if (!(o->inner_tol >= 0.0) || o->inner_max_cycles < 1 || (o->inner_monitor != 0 && o->inner_monitor != 1))
         return fail(h, JFNK_EINVAL, "bad inner tolerance options");
@@ -803,7 +819,7 @@ jfnk_status jfnk_jv(jfnk_handle* h, const double* X, double dt, const void* v, v
     if (!X || !v || !Jv || !(dt > 0.0)) return fail(h, JFNK_EINVAL, "bad arguments to jfnk_jv");
     scaling(h, X);
     eval<kModeG, double>(h, X, dt, h->G0, (double*)nullptr);
-    launch_jv_coeffs(h->Linv, h->G0, dt, h->opt.theta, h->jvP, h->jvQ, h->jvC, h->nvec, h->stream);
+    launch_jv_coeffs(h->Linv, h->G0, dt, h->opt.theta, h->jvP, h->jvQ, h->jvC, h->nvec, 2 * h->nc, h->stream);
     if (h->mixed) jv<float, float>(h, X, dt, (const float*)v, 0, (float*)Jv);
     else jv<double, double>(h, X, dt, (const double*)v, 0, (double*)Jv);
     if (delta_used) {
@@ -852,6 +868,7 @@ jfnk_status jfnk_linear_solve(jfnk_handle* h, const double* X, const double* Xn,
         stats->inner_res_mean = so.inner_n > 0 ? so.inner_sum / so.inner_n : 0.0;
         stats->inner_res_max = so.inner_max;
         stats->inner_cycles = h->inner_cycles;
+        stats->reorth_passes = so.reorth;
     }
     return so.converged ? JFNK_OK : JFNK_ENOCONV_GMRES;
 }
@@ -898,6 +915,7 @@ jfnk_status jfnk_step(jfnk_handle* h, double* X, double dt, double newton_tol, d
         for (int q = 0; q < 5; ++q) S->jv_kernel_ms[q] += so.kms[q];
         inner_sum += so.inner_sum;
         inner_n += so.inner_n;
+        S->reorth_passes += so.reorth;
         S->inner_res_max = std::max(S->inner_res_max, so.inner_max);
         if (!so.converged) gmres_fail = true;
         if (!std::isfinite(dinf)) return fail(h, JFNK_ENONFINITE, "non-finite Newton correction");

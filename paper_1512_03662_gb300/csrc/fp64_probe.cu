@@ -1,5 +1,8 @@
 // FP64 throughput probe: the measured peak that the FP64-bound stencil
-// kernels are compared against.
+// kernels are compared against; and checks, run by the tests, of two device
+// functions of the solver's kernels: the Newton-Raphson reciprocal
+// (recip_nr) against IEEE division and the integer-pipe halving
+// (half_exact) against the FP64 product.
 //
 // Every thread runs eight independent chains of fused multiply-adds
 // x <- x * a + b (one DFMA instruction, two flops each), so the FP64 pipe
@@ -9,6 +12,8 @@
 // no chain is dead code.  This is not part of the solver library: bench.py
 // loads it on its own to time the probe with CUDA events.
 #include <cuda_runtime.h>
+
+#include "common.cuh"
 
 namespace {
 
@@ -28,9 +33,39 @@ __global__ void __launch_bounds__(256) k_dfma_probe(double* out, int iters, doub
     out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void k_recip_check(const double* __restrict__ d, double* __restrict__ r, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) r[i] = jfnk::recip_nr(d[i]);
+}
+
+__global__ void k_half_check(const double* __restrict__ x, double* __restrict__ r, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) r[i] = jfnk::half_exact(x[i]);
+}
+
 }  // namespace
 
 extern "C" {
+
+// r[i] = half_exact(x[i]) for i < n (device arrays), queued on `stream`.
+int fp64_half_check(const double* x, double* r, long long n, void* stream) {
+    if (!x || !r || n <= 0) return (int)cudaErrorInvalidValue;
+    const long long blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    k_half_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, r, n);
+    return (int)cudaGetLastError();
+}
+
+// r[i] = recip_nr(d[i]) (the reciprocal of the batched inversion in the
+// residual kernels) for i < n, queued on `stream`; d and r are device
+// arrays of n doubles.
+int fp64_recip_check(const double* d, double* r, long long n, void* stream) {
+    if (!d || !r || n <= 0) return (int)cudaErrorInvalidValue;
+    const long long blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    k_recip_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
+    return (int)cudaGetLastError();
+}
 
 // DFMA instructions one launch executes per thread.
 long long fp64_probe_fma_per_thread(int iters) { return (long long)iters * kChains; }

@@ -26,6 +26,7 @@ enum {
     kSlotInvDelta = 9,   // 1/delta of the current Jv (one division, not one per thread)
     kSlotInnerB = 10,    // ||b||_2 of the finest-level SI system of the current preconditioner apply
     kSlotInnerR = 11,    // ||b - A x||_2 after its V-cycles
+    kSlotWnorm0 = 12,    // ||w||_2 of the new Arnoldi vector before Gram-Schmidt (selective second pass)
     kNumSlots = 16
 };
 
@@ -93,7 +94,7 @@ void launch_add_col(double* col, const double* other, int n, cudaStream_t s);
 // coefficients of the Jacobian-free product for one linearisation:
 // P = L^-1 / dt, Q = theta L^-1, C = L^-1 G(X)
 void launch_jv_coeffs(const double* Linv, const double* G0, double dt, double theta, double* P, double* Q, double* C,
-                      long long n, cudaStream_t s);
+                      long long n, long long u_begin, cudaStream_t s);
 
 // precond.cu
 struct MGLevel {

@@ -737,20 +737,24 @@ __global__ void k_add_col(double* col, const double* other, int n) {
     if (i < n) col[i] += other[i];
 }
 
-__global__ void k_jv_coeffs(const double* __restrict__ Linv, const double* __restrict__ G0, double idt, double theta,
-                            double* __restrict__ P, double* __restrict__ Q, double* __restrict__ C, long long n) {
+// P = L^-1/dt, Q = theta L^-1, C = L^-1 G(X) of the Jacobian-free assemble;
+// entries from u_begin on (the momentum rows, whose conserved value the
+// assemble forms as 2 rho_f u) take P = L^-1/(2 dt)
+__global__ void k_jv_coeffs(const double* __restrict__ Linv, const double* __restrict__ G0, double idt, double idt_h,
+                            double theta, double* __restrict__ P, double* __restrict__ Q, double* __restrict__ C,
+                            long long n, long long u_begin) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const double li = Linv[e];
-        P[e] = idt * li;
+        P[e] = (e < u_begin ? idt : idt_h) * li;
         Q[e] = theta * li;
         C[e] = G0[e] * li;
     }
 }
 
 void launch_jv_coeffs(const double* Linv, const double* G0, double dt, double theta, double* P, double* Q, double* C,
-                      long long n, cudaStream_t s) {
+                      long long n, long long u_begin, cudaStream_t s) {
     ++g_launch_count;
-    k_jv_coeffs<<<kRedBlocks, kBlock, 0, s>>>(Linv, G0, 1.0 / dt, theta, P, Q, C, n);
+    k_jv_coeffs<<<kRedBlocks, kBlock, 0, s>>>(Linv, G0, 1.0 / dt, 0.5 / dt, theta, P, Q, C, n, u_begin);
 }
 
 void launch_add_col(double* col, const double* other, int n, cudaStream_t s) {

@@ -119,7 +119,7 @@ __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double
             const double sq = (chil + __ldg(chi + c)) * G.hidx[d];
             fe = fma(-sq, __ldg(T + c) - Tl, fe);
         }
-        Fmh[d * nc + c] = 0.5 * fm;           // half mass flux: every consumer averages two of them
+        Fmh[d * nc + c] = half_exact(fm);     // half mass flux: every consumer averages two of them
         FE[d * nc + c] = fe;
     }
 }
@@ -203,7 +203,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
                            const double* __restrict__ Fm, const double* __restrict__ FE,
                            const double* __restrict__ Psi, const double* __restrict__ bn,
                            const double* __restrict__ G0, const double* __restrict__ Linv,
-                           const double* __restrict__ scal, int delta_slot, double dt_inv,
+                           const double* __restrict__ scal, int delta_slot, double dt_inv, double dt_inv_h,
                            double* __restrict__ outd, TO* __restrict__ outb) {
     Idx3 P;
     long long cc;
@@ -248,9 +248,12 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         o[c] = -1;
         double pl = load_cell(G, p, P, o[0], o[1], o[2]);
         double rl = load_cell(G, X, P, o[0], o[1], o[2]);
-        double rho_f = 0.5 * (rl + rho);
+        // rs = rl + rho = 2 rho_f: the 1/2 of the face mean is carried by
+        // g/2 here and by the halved 1/dt factors of the momentum rows below
+        // (exact powers of two: the results are those of rho_f itself)
+        const double rs = rl + rho;
         double Rc = -(pc - pl) * G.idx[c];
-        if ((G.gmask >> c) & 1) Rc = Rc + rho_f * G.g[c];
+        if ((G.gmask >> c) & 1) Rc = fma(rs, G.hg[c], Rc);
 #pragma unroll
         for (int d = 0; d < nd; ++d) {
             const double* ps = Psi + (c * nd + d) * nc;
@@ -265,26 +268,28 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
                 Rc = Rc - (b - a) * G.idx[d];
             }
         }
-        Uv[2 + c] = rho_f * __ldg(X + (2 + c) * nc + cc);
+        Uv[2 + c] = rs * __ldg(X + (2 + c) * nc + cc);        // 2 rho_f u
         Rv[2 + c] = Rc;
     }
 #pragma unroll
     for (int k = 0; k < 2 + nd; ++k) {
         const long long j = k * nc + cc;
         const bool wall = (k >= 2) && is_wall_slot(G, k - 2, P);
+        const double di = k >= 2 ? dt_inv_h : dt_inv;      // momentum rows hold 2 rho_f u
         if (MODE == kModeG) {
-            outd[j] = Uv[k] * dt_inv - th * Rv[k];
+            outd[j] = Uv[k] * di - th * Rv[k];
         } else if (MODE == kModeBn) {
-            outd[j] = Uv[k] * dt_inv + (1.0 - th) * Rv[k];
+            outd[j] = Uv[k] * di + (1.0 - th) * Rv[k];
         } else if (MODE == kModeRes) {
-            outd[j] = Uv[k] * dt_inv - th * Rv[k] - bn[j];
+            outd[j] = Uv[k] * di - th * Rv[k] - bn[j];
         } else if (MODE == kModeNewton) {
-            double g = Uv[k] * dt_inv - th * Rv[k];
+            double g = Uv[k] * di - th * Rv[k];
             outd[j] = g;
             outb[j] = wall ? (TO)0 : (TO)(-((g - bn[j]) * Linv[j]));
         } else {
             // kModeJv: L^-1 (G(X+dw) - G(X)) / delta with bn, G0, Linv holding
-            // Q = theta L^-1, C = L^-1 G(X) and P = L^-1/dt (launch_jv_coeffs):
+            // Q = theta L^-1, C = L^-1 G(X) and P = L^-1/dt, halved on the
+            // momentum rows (launch_jv_coeffs):
             // (U P - R Q - C) / delta, two FMAs and a product per unknown;
             // kModeJvD leaves out the 1/delta (GMRES applies it to its
             // Hessenberg column): two FMAs per unknown
@@ -452,10 +457,10 @@ void launch_assemble(const Grid& G, const double* X, const double* p, const doub
     ++g_launch_count;
     if (G.ndim == 3)
         k_assemble<3, MODE, TO><<<cl.grid, cl.block, 0, s>>>(G, X, p, Fm, FE, Psi, bn, G0, Linv, scal, slot, 1.0 / dt,
-                                                           outd, outb);
+                                                           0.5 / dt, outd, outb);
     else
         k_assemble<2, MODE, TO><<<cl.grid, cl.block, 0, s>>>(G, X, p, Fm, FE, Psi, bn, G0, Linv, scal, slot, 1.0 / dt,
-                                                           outd, outb);
+                                                           0.5 / dt, outd, outb);
 }
 #define INST(M, T)                                                                                             \
     template void launch_assemble<M, T>(const Grid&, const double*, const double*, const double*, const double*, \
