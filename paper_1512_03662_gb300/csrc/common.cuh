@@ -195,13 +195,16 @@ __device__ __forceinline__ Upw upwind_parts(double q_near, double q_far, double 
 // common case) an exponent decrement of the high word on the integer pipe,
 // with no FP64 instruction; zero, subnormal, infinite and NaN values take
 // the FP64 product, in a branch that only warps holding such a value enter.
+// (The fallback operation is volatile inline PTX so that the
+// compiler cannot evaluate it speculatively outside its branch, which
+// would put it back on the FP64 pipe for every thread.)
 __device__ __forceinline__ double half_exact(double x) {
     const int hi = __double2hiint(x);
     const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
     double r = __hiloint2double(hi - 0x00100000, __double2loint(x));
     const bool slow = (e - 2u) > 0x7fcu;          // e < 2 or e == 0x7ff
     if (__any_sync(__activemask(), slow)) {
-        if (slow) r = 0.5 * x;
+        if (slow) asm volatile("mul.rn.f64 %0, %1, 0d3FE0000000000000;" : "=d"(r) : "d"(x));
     }
     return r;
 }
@@ -256,6 +259,47 @@ __device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K]) 
     } else {
 #pragma unroll
         for (int i = 0; i < K; ++i) r[i] = 1.0 / d[i];
+    }
+}
+
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) used by
+// the float basis and the float preconditioner output: a dot product
+// accumulated as an unevaluated pair (sum, err) is as accurate as one
+// accumulated in twice the working precision (Ogita, Rump & Oishi,
+// "Accurate sum and dot product", 2005), without touching the FP64 pipe
+// inside the loop.
+struct CompF {
+    float s, e;
+};
+
+// (explicitly rounded intrinsics: the compiler must not contract these into FMAs)
+__device__ __forceinline__ void comp_add(CompF& a, float p) {
+    float t = __fadd_rn(a.s, p);
+    float bp = __fsub_rn(t, a.s);
+    a.e = __fadd_rn(a.e, __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+    a.s = t;
+}
+
+__device__ __forceinline__ void comp_fma(CompF& a, float x, float y) {
+    float p = __fmul_rn(x, y);
+    float err = fmaf(x, y, -p);
+    comp_add(a, p);
+    a.e = __fadd_rn(a.e, err);
+}
+
+// a += x^2 for a float x: compensated float pair when x is zero or its
+// square stays in the normal float range (|x| in [2^-60, 2^60)), the double
+// accumulator d otherwise (a branch that only lanes holding such a value take)
+__device__ __forceinline__ void comp_sq(CompF& a, double& d, float x) {
+    const float ax = fabsf(x);
+    const bool wide = !(ax == 0.f || (ax >= 0x1p-60f && ax < 0x1p60f));
+    comp_fma(a, wide ? 0.f : x, wide ? 0.f : x);
+    if (__any_sync(__activemask(), wide)) {
+        if (wide) {
+            double xd;
+            asm volatile("cvt.f64.f32 %0, %1;" : "=d"(xd) : "f"(x));
+            asm volatile("fma.rn.f64 %0, %1, %1, %2;" : "=d"(d) : "d"(xd), "d"(d));
+        }
     }
 }
 

@@ -47,26 +47,6 @@ __global__ void k_half_check(const double* __restrict__ x, double* __restrict__ 
 
 extern "C" {
 
-// r[i] = half_exact(x[i]) for i < n (device arrays), queued on `stream`.
-int fp64_half_check(const double* x, double* r, long long n, void* stream) {
-    if (!x || !r || n <= 0) return (int)cudaErrorInvalidValue;
-    const long long blocks = (n + 255) / 256;
-    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    k_half_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, r, n);
-    return (int)cudaGetLastError();
-}
-
-// r[i] = recip_nr(d[i]) (the reciprocal of the batched inversion in the
-// residual kernels) for i < n, queued on `stream`; d and r are device
-// arrays of n doubles.
-int fp64_recip_check(const double* d, double* r, long long n, void* stream) {
-    if (!d || !r || n <= 0) return (int)cudaErrorInvalidValue;
-    const long long blocks = (n + 255) / 256;
-    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    k_recip_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
-    return (int)cudaGetLastError();
-}
-
 // DFMA instructions one launch executes per thread.
 long long fp64_probe_fma_per_thread(int iters) { return (long long)iters * kChains; }
 

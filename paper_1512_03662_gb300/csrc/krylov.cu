@@ -14,30 +14,6 @@
 
 namespace jfnk {
 
-// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) used by
-// the float basis: a dot product accumulated as an unevaluated pair
-// (sum, err) is as accurate as one accumulated in twice the working
-// precision (Ogita, Rump & Oishi, "Accurate sum and dot product", 2005),
-// without touching the FP64 pipe inside the loop.
-struct CompF {
-    float s, e;
-};
-
-// (explicitly rounded intrinsics: the compiler must not contract these into FMAs)
-__device__ __forceinline__ void comp_add(CompF& a, float p) {
-    float t = __fadd_rn(a.s, p);
-    float bp = __fsub_rn(t, a.s);
-    a.e = __fadd_rn(a.e, __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
-    a.s = t;
-}
-
-__device__ __forceinline__ void comp_fma(CompF& a, float x, float y) {
-    float p = __fmul_rn(x, y);
-    float err = fmaf(x, y, -p);
-    comp_add(a, p);
-    a.e = __fadd_rn(a.e, err);
-}
-
 // Grid of a grid-stride reduction: as many blocks as are resident on all
 // SMs at once (one wave: no tail wave, every SM equally loaded), capped at
 // kMaxRedBlocks.  Fixed per kernel and device, so the summation order and
@@ -97,14 +73,23 @@ __global__ void k_delta(double* scal, double lambda, int pert) {
 
 void launch_delta(double* scal, double lambda, int pert, cudaStream_t s) { k_delta<<<1, 1, 0, s>>>(scal, lambda, pert); }
 
+// partial sums of x_i^2: in double for a double x; for a float x as a
+// compensated float pair per thread (comp_sq: no FP64 instruction for
+// elements of moderate size), converted to double once per thread
 template <typename T>
 __global__ void k_norm2(const T* __restrict__ x, long long n, double* __restrict__ partials) {
     __shared__ double sh[32];
     double acc = 0.0;
+    CompF accf = {0.f, 0.f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v = (double)x[i];
-        acc += v * v;
+        if (sizeof(T) == 8) {
+            const double v = (double)x[i];
+            acc += v * v;
+        } else {
+            comp_sq(accf, acc, (float)x[i]);
+        }
     }
+    if (sizeof(T) != 8) acc += (double)accf.s + (double)accf.e;
     double s = block_sum<kBlock>(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }

@@ -623,18 +623,60 @@ __global__ void k_restrict(LvlDev F, LvlDev C, const T* __restrict__ r, T* __res
     restrict_cell<T, NF, ND>(F, C, r, rhsc, xc, ic, cc, red_only, zero_xc);
 }
 
+// Residual and restriction in one pass, after a pre-smoothing sweep (the
+// colour-1 residual is zero): one thread per coarse cell evaluates the
+// residuals of its colour-0 children where the restriction needs them, in
+// the same pair order as restrict_cell, so the coarse right-hand side is
+// bitwise that of the two-kernel path, without writing and re-reading the
+// fine residual.
+template <typename T, int NF, int ND>
+__global__ void k_residual_restrict(LvlDev F, LvlDev C, const T* __restrict__ M, const T* __restrict__ K,
+                                    const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ rhsc,
+                                    int tr) {
+    // one thread per coarse cell and field: blockIdx.z runs over the coarse
+    // z index of field 0, then of field 1
+    int ic[3];
+    ic[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    ic[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    const int f = blockIdx.z / C.n[2];
+    ic[2] = blockIdx.z - f * C.n[2];
+    if (ic[0] >= C.n[0] || ic[1] >= C.n[1]) return;
+    const long long cc = lflat(C, ic[0], ic[1], ic[2]);
+    const bool cx = F.n[0] != C.n[0], cy = F.n[1] != C.n[1], cz = F.n[2] != C.n[2];
+    const int x0 = cx ? 2 * ic[0] : ic[0], y0 = cy ? 2 * ic[1] : ic[1], z0 = cz ? 2 * ic[2] : ic[2];
+    {
+        auto child = [&](int xx, int yy, int zz) -> T {
+            return ((xx + yy + zz) & 1) ? (T)0 : fine_residual<T, NF, ND>(F, M, K, x, rhs, f, xx, yy, zz, tr);
+        };
+        auto xm = [&](int yy, int zz) -> T {
+            T a = child(x0, yy, zz);
+            return cx ? (a + child(x0 + 1, yy, zz)) / (T)2 : a;
+        };
+        auto ym = [&](int zz) -> T {
+            T a = xm(y0, zz);
+            return cy ? (a + xm(y0 + 1, zz)) / (T)2 : a;
+        };
+        T a = ym(z0);
+        rhsc[(long long)f * C.nc + cc] = cz ? (a + ym(z0 + 1)) / (T)2 : a;
+    }
+}
+
 template <typename T>
 void launch_restrict(const Grid& G, int nf, MGLevel& F, MGLevel& C, cudaStream_t s, int tr, int red_only) {
-    const int compact = (red_only && F.n[0] % 2 == 0) ? 1 : 0;
-    int nx[3] = {compact ? F.n[0] / 2 : F.n[0], F.n[1], F.n[2]};
-    CellLaunch fl = cell_launch(nx);
-    MG_DISPATCH(k_residual_mg, fl.grid, fl.block, lvl(F), (const T*)F.M, (const T*)F.K, (const T*)F.x,
-                (const T*)F.rhs, (T*)F.r, tr, red_only, compact);
     CellLaunch cl = cell_launch(C.n);
-    // after a pre-smoothing sweep the coarse level starts with a zero-start
-    // half sweep, so x needs zeroing only without pre-smoothing
-    MG_DISPATCH(k_restrict, cl.grid, cl.block, lvl(F), lvl(C), (const T*)F.r, (T*)C.rhs, (T*)C.x, red_only,
-                red_only ? 0 : 1);
+    if (red_only) {
+        // after a pre-smoothing sweep the coarse level starts with a
+        // zero-start half sweep, so its x needs no zeroing
+        dim3 grid = cl.grid;
+        grid.z *= nf;
+        MG_DISPATCH(k_residual_restrict, grid, cl.block, lvl(F), lvl(C), (const T*)F.M, (const T*)F.K,
+                    (const T*)F.x, (const T*)F.rhs, (T*)C.rhs, tr);
+        return;
+    }
+    CellLaunch fl = cell_launch(F.n);
+    MG_DISPATCH(k_residual_mg, fl.grid, fl.block, lvl(F), (const T*)F.M, (const T*)F.K, (const T*)F.x,
+                (const T*)F.rhs, (T*)F.r, tr, 0, 0);
+    MG_DISPATCH(k_restrict, cl.grid, cl.block, lvl(F), lvl(C), (const T*)F.r, (T*)C.rhs, (T*)C.x, 0, 1);
 }
 template void launch_restrict<double>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
 template void launch_restrict<float>(const Grid&, int, MGLevel&, MGLevel&, cudaStream_t, int, int);
@@ -937,7 +979,11 @@ __global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int 
                               const T* __restrict__ re, const T* __restrict__ ru, const T* __restrict__ x,
                               T* __restrict__ z, double* __restrict__ partials, int ntiles) {
     __shared__ double sh[32];
+    // |z|^2: in double for a double z; for a float z as a compensated float
+    // pair (comp_sq: no FP64 conversion or FMA for elements of moderate
+    // size), converted once per thread
     double acc = 0.0;
+    CompF accf = {0.f, 0.f};
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Idx3 P;
         long long cc;
@@ -977,10 +1023,15 @@ __global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int 
 #pragma unroll
         for (int k = 0; k < 2 + ND; ++k) {
             z[k * nc + cc] = out[k];
-            double zd = (double)out[k];
-            acc += zd * zd;
+            if (sizeof(T) == 8) {
+                const double zd = (double)out[k];
+                acc += zd * zd;
+            } else {
+                comp_sq(accf, acc, (float)out[k]);
+            }
         }
     }
+    if (sizeof(T) != 8) acc += (double)accf.s + (double)accf.e;
     double s = block_sum<128>(acc, sh);
     if (thread_linear() == 0) partials[blockIdx.x] = s;
 }

@@ -32,7 +32,12 @@ __global__ void k_perturb(Grid G, const double* __restrict__ X, const TZ* __rest
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= nvec) return;
     const double delta = scal[delta_slot];
-    Xp[k] = X[k] + delta * (R[k] * (double)z[k]);
+    // R_rho = rho and R_e = e (Eq. jacobian_system_norm; k_scaling stores
+    // them as copies of X): the density and energy rows take R from X
+    // instead of reading it again
+    const double x = X[k];
+    const double r = k < 2 * G.ncell ? x : R[k];
+    Xp[k] = x + delta * (r * (double)z[k]);
 }
 
 __device__ __forceinline__ double conductivity(const Grid& G, double T) {

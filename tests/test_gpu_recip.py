@@ -77,3 +77,4 @@ def test_integer_pipe_halving_equals_the_fp64_product(probe):
     torch.cuda.synchronize()
     same = (r.view(torch.int64) == ref.view(torch.int64)) | (torch.isnan(r) & torch.isnan(ref))
     assert bool(same.all()), x[~same.cpu().numpy()][:8]
+
