@@ -407,7 +407,7 @@ def reference_main(args, ws, rank):
         secs.append(s)
     mean = sum(secs) / len(secs)
     scale = (n_small / args.n) ** 3
-    value = scale / mean
+    value = scale / mean          # steps/s of the full grid, from the sample by the cell ratio
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -415,7 +415,8 @@ def reference_main(args, ws, rank):
                        "parallelism": "replicas", "l2": "state larger than L2"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"oracle implicit step at {n_small}^3 (same construction, same dt), "
-                                       f"time scaled by the cell ratio ({args.n}/{n_small})^3"},
+                                       f"time scaled by the cell ratio ({args.n}/{n_small})^3",
+                             "seconds_per_sample": mean, "host": cpu_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -999,7 +1000,7 @@ def main():
     ap.add_argument("--study-n", type=int, default=None,
                     help="cells per direction of --study tgv (default 64) or machsweep (128)")
     ap.add_argument("--cfl", type=float, default=None, help="--study machsweep: CFL_hydro instead of 1000")
-    ap.add_argument("--ref-n", type=int, default=32,
+    ap.add_argument("--ref-n", type=int, default=64,
                     help="cells per direction of the oracle step of --impl reference")
     ap.add_argument("--cpu-n", type=int, default=64,
                     help="cells per direction of the oracle step of cpu_baseline")

@@ -191,23 +191,69 @@ __device__ __forceinline__ Upw upwind_parts(double q_near, double q_far, double 
     return u;
 }
 
-// x / 2, exactly: for a normal x whose biased exponent exceeds 1 (the
-// common case) an exponent decrement of the high word on the integer pipe,
-// with no FP64 instruction; zero, subnormal, infinite and NaN values take
-// the FP64 product, in a branch that only warps holding such a value enter.
-// (The fallback operation is volatile inline PTX so that the
-// compiler cannot evaluate it speculatively outside its branch, which
-// would put it back on the FP64 pipe for every thread.)
-__device__ __forceinline__ double half_exact(double x) {
-    const int hi = __double2hiint(x);
-    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
-    double r = __hiloint2double(hi - 0x00100000, __double2loint(x));
-    const bool slow = (e - 2u) > 0x7fcu;          // e < 2 or e == 0x7ff
-    if (__any_sync(__activemask(), slow)) {
-        if (slow) asm volatile("mul.rn.f64 %0, %1, 0d3FE0000000000000;" : "=d"(r) : "d"(x));
+// Float <-> double conversions on the integer pipe.  On sm_103a the
+// conversion instructions run on the FP64 pipe (2 per cycle per SM), and a
+// predicated-off instruction still occupies it, so these handle every
+// input in integer arithmetic, with no FP64 instruction on any path, and
+// give the bits of the conversion instructions (IEEE 754: the float->double
+// conversion is exact, double->float rounds to nearest, ties to even; NaNs
+// stay NaNs).
+
+// (double)f
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u, mag = u & 0x7fffffffu, m = u & 0x7fffffu;
+    const unsigned e = mag >> 23;
+    unsigned hi, lo;
+    if (e - 1u < 254u) {                              // normal: rebias by 1023 - 127 = 896
+        hi = sign | ((mag >> 3) + 0x38000000u);
+        lo = u << 29;
+    } else if (e == 255u) {                           // infinity or NaN (quiet)
+        hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x00080000u : 0u);
+        lo = m << 29;
+    } else if (m == 0u) {                             // zero
+        hi = sign;
+        lo = 0u;
+    } else {                                          // subnormal float: a normal double
+        const int k = 31 - __clz(m);                  // leading bit of m (value m 2^-149)
+        const unsigned long long t = ((unsigned long long)m << (52 - k)) & 0xfffffffffffffULL;
+        hi = sign | ((unsigned)(k + 874) << 20) | (unsigned)(t >> 32);
+        lo = (unsigned)t;
     }
-    return r;
+    return __hiloint2double((int)hi, (int)lo);
 }
+
+// (float)x, rounded to nearest, ties to even
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
+    unsigned b;
+    if (e - 897u <= 1150u - 897u) {                   // normal float result: keep 23 bits, round on 29
+        const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;
+        b = (((e - 896u) << 23) | m23) + ((rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u);
+    } else if (e == 0x7ffu) {                         // infinity or NaN (quiet)
+        const bool nan = (hi & 0xfffffu) | lo;
+        b = 0x7f800000u | (nan ? 0x00400000u | ((hi & 0xfffffu) << 3) | (lo >> 29) : 0u);
+    } else if (e > 1150u) {                           // beyond the float range: infinity
+        b = 0x7f800000u;
+    } else if (e >= 873u) {                           // subnormal float (or the smallest normal)
+        const unsigned long long m53 = (1ULL << 52) | ((unsigned long long)(hi & 0xfffffu) << 32) | lo;
+        const unsigned s = 926u - e;                  // 30 .. 53
+        const unsigned long long v = m53 >> s, r = m53 & ((1ULL << s) - 1ULL), half = 1ULL << (s - 1u);
+        b = (unsigned)v + ((r > half || (r == half && (v & 1ULL))) ? 1u : 0u);
+    } else {                                          // below half the smallest subnormal: zero
+        b = 0u;
+    }
+    return __uint_as_float(sign | b);
+}
+
+// between the basis precision and double
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_exact(x); }
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_rn(x); }
 
 // 1/d by Newton-Raphson iteration for the reciprocal (Markstein, IBM J.
 // Res. Dev. 34 (1990) 111-119): from the hardware approximation r0
@@ -287,20 +333,14 @@ __device__ __forceinline__ void comp_fma(CompF& a, float x, float y) {
     a.e = __fadd_rn(a.e, err);
 }
 
-// a += x^2 for a float x: compensated float pair when x is zero or its
-// square stays in the normal float range (|x| in [2^-60, 2^60)), the double
-// accumulator d otherwise (a branch that only lanes holding such a value take)
-__device__ __forceinline__ void comp_sq(CompF& a, double& d, float x) {
-    const float ax = fabsf(x);
-    const bool wide = !(ax == 0.f || (ax >= 0x1p-60f && ax < 0x1p60f));
-    comp_fma(a, wide ? 0.f : x, wide ? 0.f : x);
-    if (__any_sync(__activemask(), wide)) {
-        if (wide) {
-            double xd;
-            asm volatile("cvt.f64.f32 %0, %1;" : "=d"(xd) : "f"(x));
-            asm volatile("fma.rn.f64 %0, %1, %1, %2;" : "=d"(d) : "d"(xd), "d"(d));
-        }
-    }
+// Squares of float values of magnitude m stay normal floats when m lies in
+// [2^-60, 2^60): a thread whose largest |x| lies outside that range redoes
+// its sum of squares in double (a second loop, taken by no thread in
+// practice); otherwise the compensated float sum is exact to about 2^-44 of
+// the result.  The check runs once per thread, after the loop, so the loop
+// itself has no FP64 instruction.
+__device__ __forceinline__ bool sq_range_unsafe(float maxabs) {
+    return maxabs >= 0x1p60f || (maxabs > 0.f && maxabs < 0x1p-60f);
 }
 
 template <typename T> struct Acc { typedef double type; };

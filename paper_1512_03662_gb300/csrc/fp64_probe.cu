@@ -1,8 +1,8 @@
 // FP64 throughput probe: the measured peak that the FP64-bound stencil
-// kernels are compared against; and checks, run by the tests, of two device
+// kernels are compared against; and checks, run by the tests, of device
 // functions of the solver's kernels: the Newton-Raphson reciprocal
-// (recip_nr) against IEEE division and the integer-pipe halving
-// (half_exact) against the FP64 product.
+// (recip_nr) against IEEE division, and the integer-pipe float/double
+// conversions (f2d_exact, d2f_rn) against the conversion instructions.
 //
 // Every thread runs eight independent chains of fused multiply-adds
 // x <- x * a + b (one DFMA instruction, two flops each), so the FP64 pipe
@@ -38,14 +38,39 @@ __global__ void k_recip_check(const double* __restrict__ d, double* __restrict__
     if (i < n) r[i] = jfnk::recip_nr(d[i]);
 }
 
-__global__ void k_half_check(const double* __restrict__ x, double* __restrict__ r, long long n) {
+__global__ void k_conv_check(const double* __restrict__ x, const float* __restrict__ f, float* __restrict__ xf,
+                             double* __restrict__ fd, long long n) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) r[i] = jfnk::half_exact(x[i]);
+    if (i < n) {
+        xf[i] = jfnk::d2f_rn(x[i]);
+        fd[i] = jfnk::f2d_exact(f[i]);
+    }
 }
 
 }  // namespace
 
 extern "C" {
+
+// xf[i] = d2f_rn(x[i]) and fd[i] = f2d_exact(f[i]) for i < n (device arrays),
+// queued on `stream`.
+int fp64_conv_check(const double* x, const float* f, float* xf, double* fd, long long n, void* stream) {
+    if (!x || !f || !xf || !fd || n <= 0) return (int)cudaErrorInvalidValue;
+    const long long blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    k_conv_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, f, xf, fd, n);
+    return (int)cudaGetLastError();
+}
+
+// r[i] = recip_nr(d[i]) (the reciprocal of the batched inversion in the
+// residual kernels) for i < n, queued on `stream`; d and r are device
+// arrays of n doubles.
+int fp64_recip_check(const double* d, double* r, long long n, void* stream) {
+    if (!d || !r || n <= 0) return (int)cudaErrorInvalidValue;
+    const long long blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    k_recip_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
+    return (int)cudaGetLastError();
+}
 
 // DFMA instructions one launch executes per thread.
 long long fp64_probe_fma_per_thread(int iters) { return (long long)iters * kChains; }

@@ -74,22 +74,36 @@ __global__ void k_delta(double* scal, double lambda, int pert) {
 void launch_delta(double* scal, double lambda, int pert, cudaStream_t s) { k_delta<<<1, 1, 0, s>>>(scal, lambda, pert); }
 
 // partial sums of x_i^2: in double for a double x; for a float x as a
-// compensated float pair per thread (comp_sq: no FP64 instruction for
-// elements of moderate size), converted to double once per thread
+// compensated float pair per thread (no FP64 instruction per element),
+// converted to double once per thread, or redone in double by a thread whose
+// values are too large or too small for float squares (sq_range_unsafe)
 template <typename T>
 __global__ void k_norm2(const T* __restrict__ x, long long n, double* __restrict__ partials) {
     __shared__ double sh[32];
     double acc = 0.0;
     CompF accf = {0.f, 0.f};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float mx = 0.f;
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    for (long long i = i0; i < n; i += st) {
         if (sizeof(T) == 8) {
             const double v = (double)x[i];
             acc += v * v;
         } else {
-            comp_sq(accf, acc, (float)x[i]);
+            const float v = (float)x[i];
+            comp_fma(accf, v, v);
+            mx = fmaxf(mx, fabsf(v));
         }
     }
-    if (sizeof(T) != 8) acc += (double)accf.s + (double)accf.e;
+    if (sizeof(T) != 8) {
+        if (sq_range_unsafe(mx)) {
+            for (long long i = i0; i < n; i += st) {
+                const double v = (double)x[i];
+                acc += v * v;
+            }
+        } else {
+            acc = (double)accf.s + (double)accf.e;
+        }
+    }
     double s = block_sum<kBlock>(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }

@@ -975,25 +975,28 @@ __device__ __forceinline__ T du_at(const Grid& G, const T* C, T dt, const T* ru,
 // reducing its partial |z|^2 once: with one tile per block the block-wide
 // reduction (two barriers per 128 cells) cost a quarter of the kernel.
 template <int ND, typename T>
-__global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int nf, const T* __restrict__ rp,
+__global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, double idt_d, int nf,
+                              const T* __restrict__ rp,
                               const T* __restrict__ re, const T* __restrict__ ru, const T* __restrict__ x,
                               T* __restrict__ z, double* __restrict__ partials, int ntiles) {
     __shared__ double sh[32];
     // |z|^2: in double for a double z; for a float z as a compensated float
-    // pair (comp_sq: no FP64 conversion or FMA for elements of moderate
-    // size), converted once per thread
+    // pair (no FP64 instruction per element), converted once per thread, or
+    // redone in double from the stored z by a thread whose values are too
+    // large or too small for float squares (sq_range_unsafe)
     double acc = 0.0;
     CompF accf = {0.f, 0.f};
+    float mx = 0.f;
+    const long long nc = G.ncell;
+    const T dt = (T)dt_d, idt = (T)idt_d;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Idx3 P;
         long long cc;
         if (!cell_pos_tile(G.n, tile, P, cc)) continue;
-        const long long nc = G.ncell;
-        const T dt = (T)dt_d;
         const long long mi = mg0(G, P);
         const T dp = x[mi];
         T de;
-        if (nf == 1) de = dt * (re[cc] + (dp * (T)(1.0 / dt_d) - rp[cc]) * C[PcCde * nc + cc]);
+        if (nf == 1) de = dt * (re[cc] + (dp * idt - rp[cc]) * C[PcCde * nc + cc]);
         else de = x[nc + mi];
         T du[ND];
 #pragma unroll
@@ -1027,11 +1030,28 @@ __global__ void k_precond_out(Grid G, const T* __restrict__ C, double dt_d, int 
                 const double zd = (double)out[k];
                 acc += zd * zd;
             } else {
-                comp_sq(accf, acc, (float)out[k]);
+                const float zf = (float)out[k];
+                comp_fma(accf, zf, zf);
+                mx = fmaxf(mx, fabsf(zf));
             }
         }
     }
-    if (sizeof(T) != 8) acc += (double)accf.s + (double)accf.e;
+    if (sizeof(T) != 8) {
+        if (sq_range_unsafe(mx)) {
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                Idx3 P;
+                long long cc;
+                if (!cell_pos_tile(G.n, tile, P, cc)) continue;
+#pragma unroll
+                for (int k = 0; k < 2 + ND; ++k) {
+                    const double zd = (double)z[k * nc + cc];
+                    acc += zd * zd;
+                }
+            }
+        } else {
+            acc = (double)accf.s + (double)accf.e;
+        }
+    }
     double s = block_sum<128>(acc, sh);
     if (thread_linear() == 0) partials[blockIdx.x] = s;
 }
@@ -1061,9 +1081,11 @@ int launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp
     if (g > ntiles) g = ntiles;
     ++g_launch_count;
     if (G.ndim == 3)
-        k_precond_out<3, T><<<g, cl.block, 0, s>>>(G, C, dt, nf, rp, re, ru, (const T*)L0.x, z, partials, ntiles);
+        k_precond_out<3, T><<<g, cl.block, 0, s>>>(G, C, dt, 1.0 / dt, nf, rp, re, ru, (const T*)L0.x, z, partials,
+                                                   ntiles);
     else
-        k_precond_out<2, T><<<g, cl.block, 0, s>>>(G, C, dt, nf, rp, re, ru, (const T*)L0.x, z, partials, ntiles);
+        k_precond_out<2, T><<<g, cl.block, 0, s>>>(G, C, dt, 1.0 / dt, nf, rp, re, ru, (const T*)L0.x, z, partials,
+                                                   ntiles);
     return g;
 }
 template int launch_precond_out<double>(const Grid&, const double*, double, int, const double*, const double*,

@@ -37,7 +37,7 @@ __global__ void k_perturb(Grid G, const double* __restrict__ X, const TZ* __rest
     // instead of reading it again
     const double x = X[k];
     const double r = k < 2 * G.ncell ? x : R[k];
-    Xp[k] = x + delta * (r * (double)z[k]);
+    Xp[k] = x + delta * (r * to_f64(z[k]));
 }
 
 __device__ __forceinline__ double conductivity(const Grid& G, double T) {
@@ -124,7 +124,7 @@ __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double
             const double sq = (chil + __ldg(chi + c)) * G.hidx[d];
             fe = fma(-sq, __ldg(T + c) - Tl, fe);
         }
-        Fmh[d * nc + c] = half_exact(fm);     // half mass flux: every consumer averages two of them
+        Fmh[d * nc + c] = 0.5 * fm;           // half mass flux: every consumer averages two of them
         FE[d * nc + c] = fe;
     }
 }
@@ -143,9 +143,11 @@ __device__ __forceinline__ double load_face_up(const Grid& G, const double* f, i
     return load_cell(G, f, P, o[0], o[1], o[2]);
 }
 
+// 128-thread blocks, at least 10 resident per SM: 48 registers (no spills)
+// instead of 54, 40 warps per SM instead of 36
 template <int ND>
-__global__ void k_mom_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ Fmh,
-                             double* __restrict__ Psi) {
+__global__ void __launch_bounds__(128, 10) k_mom_fluxes(Grid G, const double* __restrict__ X,
+                                                        const double* __restrict__ Fmh, double* __restrict__ Psi) {
     Idx3 P;
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
@@ -290,7 +292,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         } else if (MODE == kModeNewton) {
             double g = Uv[k] * di - th * Rv[k];
             outd[j] = g;
-            outb[j] = wall ? (TO)0 : (TO)(-((g - bn[j]) * Linv[j]));
+            outb[j] = wall ? (TO)0 : from_f64<TO>(-((g - bn[j]) * Linv[j]));
         } else {
             // kModeJv: L^-1 (G(X+dw) - G(X)) / delta with bn, G0, Linv holding
             // Q = theta L^-1, C = L^-1 G(X) and P = L^-1/dt, halved on the
@@ -300,7 +302,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
             // Hessenberg column): two FMAs per unknown
             const double q = fma(Rv[k], bn[j], G0[j]);
             const double d = fma(Uv[k], Linv[j], -q);
-            outb[j] = wall ? (TO)0 : (TO)(MODE == kModeJv ? d * inv_delta : d);
+            outb[j] = wall ? (TO)0 : from_f64<TO>(MODE == kModeJv ? d * inv_delta : d);
         }
     }
 }

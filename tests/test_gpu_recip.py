@@ -56,25 +56,50 @@ def test_newton_raphson_reciprocal_is_within_one_ulp(probe):
     assert frac_exact > 0.9
 
 
-def test_integer_pipe_halving_equals_the_fp64_product(probe):
-    """half_exact (the half mass flux of k_face_fluxes, an exponent decrement
-    on the integer pipe) is bit-for-bit x * 0.5 for normal values of every
-    exponent, and falls back to the product for zeros, subnormals, the
-    smallest normal binade, infinities and NaN."""
-    probe.fp64_half_check.restype = ctypes.c_int
-    probe.fp64_half_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
-    rng = np.random.default_rng(12)
-    n = 1 << 20
-    x = rng.choice([-1.0, 1.0], n) * np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-1074, 1024, n))
-    tiny = np.finfo(np.float64).tiny
-    special = np.array([0.0, -0.0, tiny, -tiny, 2 * tiny, np.nextafter(2 * tiny, 0), 5e-324, -5e-324,
-                        np.nextafter(tiny, 0), np.inf, -np.inf, np.nan, np.finfo(np.float64).max, 1.0, -3.5])
-    x[:len(special)] = special
-    xg = torch.as_tensor(x, device="cuda")
-    r = torch.empty_like(xg)
-    assert probe.fp64_half_check(ctypes.c_void_p(xg.data_ptr()), ctypes.c_void_p(r.data_ptr()), n, None) == 0
-    ref = xg * 0.5
-    torch.cuda.synchronize()
-    same = (r.view(torch.int64) == ref.view(torch.int64)) | (torch.isnan(r) & torch.isnan(ref))
-    assert bool(same.all()), x[~same.cpu().numpy()][:8]
 
+def test_integer_pipe_conversions_equal_the_conversion_instructions(probe):
+    """d2f_rn (the float output of the Jacobian-free assemble) and f2d_exact
+    (the float Krylov vector read by the perturbation kernel) give the bits
+    of the hardware conversions for every class of input: normal values,
+    half-way cases (ties to even), carries into the exponent, overflow to
+    infinity, float subnormals on both sides, zeros, infinities; NaN stays
+    NaN."""
+    probe.fp64_conv_check.restype = ctypes.c_int
+    probe.fp64_conv_check.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p]
+    rng = np.random.default_rng(13)
+    n = 1 << 21
+    x = rng.choice([-1.0, 1.0], n) * np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-160, 140, n))
+    # half-way doubles between two floats (ties) and their neighbours, among
+    # normal floats and among float subnormals
+    m = rng.integers(1 << 23, 1 << 24, 4096).astype(np.float64)
+    ties = np.ldexp(m + 0.5, rng.integers(-140, 100, 4096) - 23)
+    sub = np.ldexp(rng.integers(0, 1 << 23, 4096).astype(np.float64) + 0.5, -149)
+    x[:4096] = ties
+    x[4096:8192] = np.nextafter(ties, np.inf)
+    x[8192:12288] = np.nextafter(ties, -np.inf)
+    x[12288:16384] = sub
+    x[16384:20480] = -np.nextafter(sub, np.inf)
+    fmax = float(np.finfo(np.float32).max)
+    special = np.array([0.0, -0.0, fmax, -fmax, fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -24), 2.0 ** 128,
+                        2.0 ** -126, 2.0 ** -127, 2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -151, 2.0 ** -151, 1e-320,
+                        np.inf, -np.inf, np.nan, np.nextafter(2.0 ** -126, 0.0), (2.0 - 2.0 ** -23) * 2.0 ** 127,
+                        (2.0 - 2.0 ** -24) * 2.0 ** -127, 1e300, -1e-300])
+    x[20480:20480 + len(special)] = special
+    f = (rng.choice([-1.0, 1.0], n) * np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-149, 128, n))).astype(np.float32)
+    f[:4096] = (rng.integers(1, 1 << 23, 4096) * np.float64(2.0 ** -149)).astype(np.float32)   # subnormals
+    fspecial = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-45, -1e-45, 1.17549435e-38, 5.877472e-39,
+                         3.4028235e38], dtype=np.float32)
+    f[4096:4096 + len(fspecial)] = fspecial
+    xg = torch.as_tensor(x, device="cuda")
+    fg = torch.as_tensor(f, device="cuda")
+    xf = torch.empty(n, dtype=torch.float32, device="cuda")
+    fd = torch.empty(n, dtype=torch.float64, device="cuda")
+    assert probe.fp64_conv_check(ctypes.c_void_p(xg.data_ptr()), ctypes.c_void_p(fg.data_ptr()),
+                                 ctypes.c_void_p(xf.data_ptr()), ctypes.c_void_p(fd.data_ptr()), n, None) == 0
+    ref_f = xg.float()
+    ref_d = fg.double()
+    torch.cuda.synchronize()
+    same_f = (xf.view(torch.int32) == ref_f.view(torch.int32)) | (torch.isnan(xf) & torch.isnan(ref_f))
+    same_d = (fd.view(torch.int64) == ref_d.view(torch.int64)) | (torch.isnan(fd) & torch.isnan(ref_d))
+    assert bool(same_f.all()), x[~same_f.cpu().numpy()][:8]
+    assert bool(same_d.all()), f[~same_d.cpu().numpy()][:8]

@@ -49,3 +49,14 @@ def test_product_path_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(jf, "_lib", None)
     with pytest.raises(RuntimeError):
         jf.lib()
+
+
+def test_probe_library_exports_what_the_bench_and_tests_call():
+    """libfp64probe.so (the FP64 peak probe of bench.py and the device
+    function checks of the GPU tests) builds and loads without a GPU."""
+    from paper_1512_03662_gb300 import build
+    build.build()
+    import ctypes
+    L = ctypes.CDLL(build.PROBE_LIB)
+    for n in ("fp64_probe_launch", "fp64_probe_fma_per_thread", "fp64_recip_check", "fp64_conv_check"):
+        assert hasattr(L, n), n
