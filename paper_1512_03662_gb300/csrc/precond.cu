@@ -144,48 +144,48 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
     }
     const long long mi = mg0(G, P);
     if (nf == 1) {
-        M[mi] = (T)(idt * ibpp);
+        M[mi] = from_f64<T>(idt * ibpp);
     } else {
-        M[0 * nc + mi] = (T)(b00 * idt);
-        M[1 * nc + mi] = (T)(b01 * idt);
-        M[2 * nc + mi] = (T)(b10 * idt);
-        M[3 * nc + mi] = (T)(b11 * idt);
+        M[0 * nc + mi] = from_f64<T>(b00 * idt);
+        M[1 * nc + mi] = from_f64<T>(b01 * idt);
+        M[2 * nc + mi] = from_f64<T>(b10 * idt);
+        M[3 * nc + mi] = from_f64<T>(b11 * idt);
     }
     const double chi0 = (G.has_cond) ? conductivity_si(G, G.gm1 * e) : 0.0;
     const double dpdrho = G.gm1 * e, dpde = G.gm1 * rho;
-    C[PcLr * nc + cc] = (T)L[cc];
-    C[PcLE * nc + cc] = (T)L[nc + cc];
-    C[PcInvRho * nc + cc] = (T)irho;
-    C[PcE * nc + cc] = (T)E;
-    C[PcDpdrho * nc + cc] = (T)dpdrho;
-    C[PcDpde * nc + cc] = (T)dpde;
-    C[PcInvDpdrho * nc + cc] = (T)(G.igm1 * ie);
-    C[PcCde * nc + cc] = (T)(G.igamma * irho);
+    C[PcLr * nc + cc] = from_f64<T>(L[cc]);
+    C[PcLE * nc + cc] = from_f64<T>(L[nc + cc]);
+    C[PcInvRho * nc + cc] = from_f64<T>(irho);
+    C[PcE * nc + cc] = from_f64<T>(E);
+    C[PcDpdrho * nc + cc] = from_f64<T>(dpdrho);
+    C[PcDpde * nc + cc] = from_f64<T>(dpde);
+    C[PcInvDpdrho * nc + cc] = from_f64<T>(G.igm1 * ie);
+    C[PcCde * nc + cc] = from_f64<T>(G.igamma * irho);
     // r_p = Pr r_rho + PE r_E - dpde <u.r_u>: first row of dV/dU in the
     // product form printed in Sect. 3.2 (no cancellation between terms)
     const double Eir = E * irho;
     const double Pr = dpdrho - dpde * Eir, PE = dpde * irho;
-    C[PcPr * nc + cc] = (T)Pr;
-    C[PcPE * nc + cc] = (T)PE;
+    C[PcPr * nc + cc] = from_f64<T>(Pr);
+    C[PcPE * nc + cc] = from_f64<T>(PE);
     if (sizeof(T) == 8) {
-        C[PcQ0 * nc + cc] = (T)b00;
+        C[PcQ0 * nc + cc] = from_f64<T>(b00);
         if (nf == 2) {
-            C[PcQ1 * nc + cc] = (T)b01;
-            C[PcQ2 * nc + cc] = (T)b10;
-            C[PcQ3 * nc + cc] = (T)b11;
+            C[PcQ1 * nc + cc] = from_f64<T>(b01);
+            C[PcQ2 * nc + cc] = from_f64<T>(b10);
+            C[PcQ3 * nc + cc] = from_f64<T>(b11);
         }
     } else {
         // rhs = B^-1 (r_p, r_e) with r_e = (r_E - E r_rho)/rho - <u.r_u>,
         // folded in double (no cancellation in FP32)
-        C[PcQ0 * nc + cc] = (T)(b00 * Pr - b01 * Eir);
-        C[PcQ1 * nc + cc] = (T)(b00 * PE + b01 * irho);
-        C[PcQ2 * nc + cc] = (T)(b00 * dpde + b01);
-        C[PcQ3 * nc + cc] = (T)(b10 * Pr - b11 * Eir);
-        C[PcQ4 * nc + cc] = (T)(b10 * PE + b11 * irho);
-        C[PcQ5 * nc + cc] = (T)(b10 * dpde + b11);
+        C[PcQ0 * nc + cc] = from_f64<T>(b00 * Pr - b01 * Eir);
+        C[PcQ1 * nc + cc] = from_f64<T>(b00 * PE + b01 * irho);
+        C[PcQ2 * nc + cc] = from_f64<T>(b00 * dpde + b01);
+        C[PcQ3 * nc + cc] = from_f64<T>(b10 * Pr - b11 * Eir);
+        C[PcQ4 * nc + cc] = from_f64<T>(b10 * PE + b11 * irho);
+        C[PcQ5 * nc + cc] = from_f64<T>(b10 * dpde + b11);
     }
-    C[PcRinvR * nc + cc] = (T)Rinv[cc];
-    C[PcRinvE * nc + cc] = (T)Rinv[nc + cc];
+    C[PcRinvR * nc + cc] = from_f64<T>(Rinv[cc]);
+    C[PcRinvE * nc + cc] = from_f64<T>(Rinv[nc + cc]);
 #pragma unroll
     for (int c = 0; c < ND; ++c) {
         const bool wall = is_wall_slot(G, c, P);
@@ -193,18 +193,18 @@ __global__ void k_pc_setup(Grid G, const double* __restrict__ X, const double* _
         o[c] = -1;
         const double irhof = inv[3 + c];
         const double m = (wall || G.n[c] == 1) ? 0.0 : 1.0;
-        K[(0 * ND + c) * nc + mi] = (T)(m * irhof);
+        K[(0 * ND + c) * nc + mi] = from_f64<T>(m * irhof);
         if (nf == 2) {
             double chil = 0.0;
             if (G.has_cond) chil = conductivity_si(G, G.gm1 * e_internal_at(G, X, P, o[0], o[1], o[2]));
-            K[(1 * ND + c) * nc + mi] = (T)(m * (0.5 * (chil + chi0)) * G.gm1);
+            K[(1 * ND + c) * nc + mi] = from_f64<T>(m * (0.5 * (chil + chi0)) * G.gm1);
         }
         const double u = wall ? 0.0 : X[(2 + c) * nc + cc];
-        C[(PcLu + c) * nc + cc] = (T)L[(2 + c) * nc + cc];
-        C[(PcU + c) * nc + cc] = (T)u;
-        C[(PcInvRhof + c) * nc + cc] = (T)(wall ? 0.0 : irhof);
-        C[(PcThf + c) * nc + cc] = (T)(wall ? 0.0 : G.theta * G.idx[c] * irhof);
-        C[(PcRinvU + c) * nc + cc] = (T)Rinv[(2 + c) * nc + cc];
+        C[(PcLu + c) * nc + cc] = from_f64<T>(L[(2 + c) * nc + cc]);
+        C[(PcU + c) * nc + cc] = from_f64<T>(u);
+        C[(PcInvRhof + c) * nc + cc] = from_f64<T>(wall ? 0.0 : irhof);
+        C[(PcThf + c) * nc + cc] = from_f64<T>(wall ? 0.0 : G.theta * G.idx[c] * irhof);
+        C[(PcRinvU + c) * nc + cc] = from_f64<T>(Rinv[(2 + c) * nc + cc]);
     }
 }
 
@@ -235,14 +235,14 @@ __global__ void k_pc_rescale(Grid G, const double* __restrict__ L, const double*
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
     const long long nc = G.ncell;
-    C[PcLr * nc + cc] = (T)L[cc];
-    C[PcLE * nc + cc] = (T)L[nc + cc];
-    C[PcRinvR * nc + cc] = (T)Rinv[cc];
-    C[PcRinvE * nc + cc] = (T)Rinv[nc + cc];
+    C[PcLr * nc + cc] = from_f64<T>(L[cc]);
+    C[PcLE * nc + cc] = from_f64<T>(L[nc + cc]);
+    C[PcRinvR * nc + cc] = from_f64<T>(Rinv[cc]);
+    C[PcRinvE * nc + cc] = from_f64<T>(Rinv[nc + cc]);
 #pragma unroll
     for (int c = 0; c < ND; ++c) {
-        C[(PcLu + c) * nc + cc] = (T)L[(2 + c) * nc + cc];
-        C[(PcRinvU + c) * nc + cc] = (T)Rinv[(2 + c) * nc + cc];
+        C[(PcLu + c) * nc + cc] = from_f64<T>(L[(2 + c) * nc + cc]);
+        C[(PcRinvU + c) * nc + cc] = from_f64<T>(Rinv[(2 + c) * nc + cc]);
     }
 }
 
