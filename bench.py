@@ -49,6 +49,9 @@ ETA = 1e-4
 KERNEL_COUNTS_HASH = "63cad653e4f26f94"
 FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 6.0, "face_fluxes": 83.0, "mom_fluxes": 114.0, "assemble": 94.9}
 FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 70.0, "mom_fluxes": 93.0, "assemble": 62.9}
+# every instruction the FP64 pipe executed (DADD/DMUL/DFMA, conversions,
+# the reciprocal approximation, ...), same capture
+FP64_PIPE_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 73.0, "mom_fluxes": 102.0, "assemble": 62.9}
 # DRAM bytes per cell per launch from the same capture (dram__bytes_read +
 # dram__bytes_write); at 128^3 part of the reads hit the 129 MB L2, so these
 # are lower bounds for 256^3 (where the algorithmic bytes below apply).
@@ -1186,6 +1189,8 @@ def main():
                 "traffic_note": "ncu DRAM bytes of a 128^3 launch scaled by the cell ratio",
                 "peak_src": peak_src, "counts_stale": stale, "counts_hash": KERNEL_COUNTS_HASH,
                 "fp64_inst_per_cell": FP64_INST_PER_CELL[name],
+                "fp64_pipe_inst_per_cell": FP64_PIPE_INST_PER_CELL[name],
+                "pipe_frac": FP64_PIPE_INST_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e12 / peak_tinst,
                 "achieved_tflops": achieved_tflops, "peak_tflops": peak_tflops,
                 "frac_tflops": achieved_tflops / peak_tflops,
                 "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"],
