@@ -194,10 +194,12 @@ __global__ void k_vjp_assemble(Grid G, const double* __restrict__ X, const doubl
 }
 
 // --------------------------------------------------------------------------
-// reverse of k_mom_fluxes
+// reverse of k_mom_fluxes (Fm: the forward mass fluxes; m is the carrying
+// mean of two of them, which the adjoint buffers below differentiate as the
+// sum of two half fluxes)
 // --------------------------------------------------------------------------
 template <int ND>
-__global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __restrict__ Fmh, AdjBufs A) {
+__global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __restrict__ Fm, AdjBufs A) {
     Idx3 P;
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
@@ -216,7 +218,7 @@ __global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __
             if (c == d) {
                 long long ju;
                 const bool hasup = up_slot(G, c, P, ju);
-                m = Fmh[c * nc + cc] + (hasup ? Fmh[c * nc + ju] : 0.0);
+                m = 0.5 * (Fm[c * nc + cc] + (hasup ? Fm[c * nc + ju] : 0.0));
                 jm1 = c * nc + cc;
                 jm2 = hasup ? c * nc + ju : -1;
                 const bool left = nonneg(m);
@@ -227,7 +229,7 @@ __global__ void k_vjp_mom(Grid G, const double* __restrict__ X, const double* __
                 int o[3] = {0, 0, 0};
                 o[c] = -1;
                 const long long jl = cell_slot(G, P, o[0], o[1], o[2]);
-                m = Fmh[d * nc + jl] + Fmh[d * nc + cc];
+                m = 0.5 * (Fm[d * nc + jl] + Fm[d * nc + cc]);
                 jm1 = d * nc + jl;
                 jm2 = d * nc + cc;
                 const bool left = nonneg(m);
@@ -393,7 +395,7 @@ __global__ void k_dRdK0_dot(Grid G, const double* __restrict__ T, const double* 
         else KERNEL<2><<<cl_.grid, cl_.block, 0, s>>>(__VA_ARGS__);                       \
     } while (0)
 
-void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* chi, const double* Fmh,
+void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* chi, const double* Fm,
                 const double* w, double a_u, double b_r, double* adj, double* Xb, cudaStream_t s) {
     const long long nc = G.ncell, nd = G.ndim;
     AdjBufs A;
@@ -408,7 +410,7 @@ void launch_vjp(const Grid& G, const double* X, const double* p, const double* T
     launch_zero<double>(adj, nadj, s);
     launch_zero<double>(Xb, (2 + nd) * nc, s);
     CELL_LAUNCH_A(k_vjp_assemble, G, X, p, w, a_u, b_r, A);
-    CELL_LAUNCH_A(k_vjp_mom, G, X, Fmh, A);
+    CELL_LAUNCH_A(k_vjp_mom, G, X, Fm, A);
     CELL_LAUNCH_A(k_vjp_face, G, X, p, T, chi, A);
     CELL_LAUNCH_A(k_vjp_eos, G, X, T, A);
 }

@@ -161,7 +161,7 @@ int launch_precond_out(const Grid& G, const T* C, double dt, int nf, const T* rp
                        const MGLevel& L0, T* z, double* partials, cudaStream_t s);
 
 // adjoint.cu
-// y = (a dU/dX + b dR/dX)^T w at X (p, T, chi and half mass fluxes of X precomputed);
+// y = (a dU/dX + b dR/dX)^T w at X (p, T, chi and mass fluxes of X precomputed);
 // adj: vjp_scratch_doubles(G) doubles of scratch
 void launch_vjp(const Grid& G, const double* X, const double* p, const double* T, const double* chi, const double* Fmh,
                 const double* w, double a_u, double b_r, double* adj, double* Xb, cudaStream_t s);

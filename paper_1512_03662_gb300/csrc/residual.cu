@@ -12,7 +12,9 @@
 //   k_face_fluxes  mass flux Fm_d and energy flux FE_d (advective part minus
 //                  conduction) on the lower face of every cell, per direction
 //   k_mom_fluxes   momentum fluxes Psi_cd: for c == d at cell centres, for
-//                  c != d on the edges between faces
+//                  c != d on the edges between faces; stored doubled (carried
+//                  by the sum of two mass fluxes, not their mean: exact, and
+//                  the assemble takes the 1/2 into 1/(2 dx))
 //   k_assemble     divergences, sources, U(X) and the requested combination
 //
 // Reconstruction (van Leer 1974): slope 2ab/(a+b) if ab > 0 else 0; the
@@ -76,7 +78,7 @@ __global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__
 
 template <int ND>
 __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ p,
-                              const double* __restrict__ T, const double* __restrict__ chi, double* __restrict__ Fmh,
+                              const double* __restrict__ T, const double* __restrict__ chi, double* __restrict__ Fm,
                               double* __restrict__ FE) {
     Idx3 P;
     long long c;
@@ -124,7 +126,7 @@ __global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double
             const double sq = (chil + __ldg(chi + c)) * G.hidx[d];
             fe = fma(-sq, __ldg(T + c) - Tl, fe);
         }
-        Fmh[d * nc + c] = 0.5 * fm;           // half mass flux: every consumer averages two of them
+        Fm[d * nc + c] = fm;                  // mass flux (every consumer takes half the sum of two)
         FE[d * nc + c] = fe;
     }
 }
@@ -147,7 +149,7 @@ __device__ __forceinline__ double load_face_up(const Grid& G, const double* f, i
 // instead of 54, 40 warps per SM instead of 36
 template <int ND>
 __global__ void __launch_bounds__(128, 10) k_mom_fluxes(Grid G, const double* __restrict__ X,
-                                                        const double* __restrict__ Fmh, double* __restrict__ Psi) {
+                                                        const double* __restrict__ Fm, double* __restrict__ Psi) {
     Idx3 P;
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
@@ -165,8 +167,8 @@ __global__ void __launch_bounds__(128, 10) k_mom_fluxes(Grid G, const double* __
             int o[3] = {0, 0, 0};
             if (c == d) {
                 // flux at the cell centre between faces i and i+1 along c, carried
-                // by the mean of the two mass fluxes (stored halved)
-                m = __ldg(Fmh + c * nc + cc) + load_face_up(G, Fmh + c * nc, c, P);
+                // by the mean of the two mass fluxes (here their sum: Psi doubled)
+                m = __ldg(Fm + c * nc + cc) + load_face_up(G, Fm + c * nc, c, P);
                 o[c] = -1; const double um = load_normal(G, uc, c, P, o[0], o[1], o[2]);
                 const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
                 o[c] = 1;  const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(128, 10) k_mom_fluxes(Grid G, const double* __
             } else {
                 // flux on the edge between c-face i_c and d-face i_d
                 o[c] = -1;
-                m = load_Fm_cell(G, Fmh + d * nc, P, o[0], o[1], o[2]) + __ldg(Fmh + d * nc + cc);
+                m = load_Fm_cell(G, Fm + d * nc, P, o[0], o[1], o[2]) + __ldg(Fm + d * nc + cc);
                 o[c] = 0;
                 o[d] = -2; const double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
                 o[d] = -1; const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
@@ -228,7 +230,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
         const double* fed = FE + d * nc;
         double fm0 = __ldg(fmd + cc), fm1 = load_face_up(G, fmd, d, P);
         double fe0 = __ldg(fed + cc), fe1 = load_face_up(G, fed, d, P);
-        Rr = Rr - (fm1 - fm0) * G.tidx[d];                  // Fm stored halved
+        Rr = Rr - (fm1 - fm0) * G.idx[d];
         RE = RE - (fe1 - fe0) * G.idx[d];
         if (G.energy_form == 0) {
             const double* ud = X + (2 + d) * nc;
@@ -238,7 +240,7 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
             double u1 = load_normal(G, ud, d, P, o[0], o[1], o[2]);
             divu = divu + (u1 - u0) * G.idx[d];
         } else if ((G.gmask >> d) & 1) {
-            RE = RE + G.g[d] * (fm0 + fm1);
+            RE = RE + G.hg[d] * (fm0 + fm1);
         }
     }
     const double pc = __ldg(p + cc);
@@ -268,11 +270,11 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
             if (c == d) {
                 b = __ldg(ps + cc);
                 a = load_cell(G, ps, P, o[0], o[1], o[2]);      // centre i-1 along c
-                Rc = Rc - (b - a) * G.idx[c];
+                Rc = Rc - (b - a) * G.hidx[c];              // Psi stored doubled
             } else {
                 a = __ldg(ps + cc);
                 b = load_face_up(G, ps, d, P);
-                Rc = Rc - (b - a) * G.idx[d];
+                Rc = Rc - (b - a) * G.hidx[d];
             }
         }
         Uv[2 + c] = rs * __ldg(X + (2 + c) * nc + cc);        // 2 rho_f u
