@@ -41,22 +41,26 @@ ETA = 1e-4
 # FP64 work per cell of one residual evaluation inside Jv, per kernel (3D,
 # internal energy, gravity, conduction, FP32 Krylov vectors), measured with
 # the ncu thread-instruction counters of a 128^3 capture (profiles/
-# jv_kernels_128cubed.md): flops = dadd + dmul + 2 dfma, instructions =
-# dadd + dmul + dfma, both divided by the cell count.  Division sequences are
-# counted as the DFMA/DMUL/DADD instructions they execute.
+# jv_kernels_128cubed.md), divided by the cell count:
+#   FP64_INST_PER_CELL       DADD + DMUL + DFMA on the FP64 pipe
+#   FP64_PIPE_INST_PER_CELL  every instruction the FP64 pipe executed
+#                            (with the reciprocal approximation, ...)
+#   INT_PIPE_OPS_PER_CELL    the correctly rounded FP64 products the flux
+#                            kernels form on the integer pipes (emu64.cuh),
+#                            counted from the source
+#   FP64_FLOPS_PER_CELL      dadd + dmul + 2 dfma + the integer-pipe products
 # KERNEL_COUNTS_HASH is kernel_source_hash() of the sources those counts were
 # measured on.
-KERNEL_COUNTS_HASH = "97b54dcbddcfbccc"
-FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 6.0, "face_fluxes": 80.0, "mom_fluxes": 114.0, "assemble": 94.9}
-FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 67.0, "mom_fluxes": 93.0, "assemble": 62.9}
-# every instruction the FP64 pipe executed (DADD/DMUL/DFMA, conversions,
-# the reciprocal approximation, ...), same capture
-FP64_PIPE_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 70.0, "mom_fluxes": 102.0, "assemble": 62.9}
+KERNEL_COUNTS_HASH = "45abbf35d2111f25"
+FP64_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 45.0, "mom_fluxes": 57.0, "assemble": 61.0}
+FP64_PIPE_INST_PER_CELL = {"perturb": 10.0, "eos": 6.0, "face_fluxes": 49.0, "mom_fluxes": 66.0, "assemble": 61.0}
+INT_PIPE_OPS_PER_CELL = {"perturb": 0.0, "eos": 0.0, "face_fluxes": 24.0, "mom_fluxes": 36.0, "assemble": 7.0}
+FP64_FLOPS_PER_CELL = {"perturb": 15.0, "eos": 6.0, "face_fluxes": 90.0, "mom_fluxes": 114.0, "assemble": 100.0}
 # DRAM bytes per cell per launch from the same capture (dram__bytes_read +
 # dram__bytes_write); at 128^3 part of the reads hit the 129 MB L2, so these
 # are lower bounds for 256^3 (where the algorithmic bytes below apply).
-DRAM_BYTES_PER_CELL_128 = {"perturb": 112.2, "eos": 17.0, "face_fluxes": 86.2, "mom_fluxes": 98.4,
-                           "assemble": 306.3}
+DRAM_BYTES_PER_CELL_128 = {"perturb": 112.1, "eos": 17.0, "face_fluxes": 86.9, "mom_fluxes": 101.0,
+                           "assemble": 305.9}
 JV_KERNELS = ["perturb", "eos", "face_fluxes", "mom_fluxes", "assemble"]
 # Algorithmic HBM bytes per cell of one launch of each Jv kernel (3D, FP64
 # state, FP32 Krylov vectors; each array the kernel must touch read or
@@ -1175,6 +1179,7 @@ def main():
     else:
         peak_tinst, peak_tflops = FP64_PEAK_TINST, FP64_PEAK_TFLOPS
         peak_src = "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz (probe failed)"
+    ops_rate = (FP64_INST_PER_CELL[name] + INT_PIPE_OPS_PER_CELL[name]) * wl.ncell / (per_launch_ms / 1e3) / 1e12
     # the whole Jacobian-free product: FP64 instructions of its five kernels
     # over their summed device time
     jv_inst = sum(FP64_INST_PER_CELL[k] for k in JV_KERNELS) * wl.ncell * njv
@@ -1182,7 +1187,10 @@ def main():
     # The kernel is bound by the FP64 pipe, which issues one DADD, DMUL or DFMA
     # per lane slot whatever its flop count, so the roofline is stated in FP64
     # instructions per second against the measured issue rate; the flop rate
-    # (DFMA = 2) is reported beside it.
+    # (DFMA = 2) is reported beside it.  The products the kernel forms on the
+    # integer pipes do not occupy the FP64 pipe: "fp64_ops_rate" counts them
+    # with the FP64-pipe arithmetic, which is why it can exceed the FP64 pipe's
+    # own peak ("ops_vs_fp64_peak").
     roofline = {"bound": "alu", "kernel": f"k_{name}", "achieved": tinst, "peak": peak_tinst,
                 "unit": "T FP64 inst/s", "frac": tinst / peak_tinst,
                 "traffic": None if stale else DRAM_BYTES_PER_CELL_128[name] * 128 ** 3 * scale,
@@ -1190,12 +1198,15 @@ def main():
                 "peak_src": peak_src, "counts_stale": stale, "counts_hash": KERNEL_COUNTS_HASH,
                 "fp64_inst_per_cell": FP64_INST_PER_CELL[name],
                 "fp64_pipe_inst_per_cell": FP64_PIPE_INST_PER_CELL[name],
+                "int_pipe_ops_per_cell": INT_PIPE_OPS_PER_CELL[name],
+                "fp64_ops_rate": ops_rate, "ops_vs_fp64_peak": ops_rate / peak_tinst,
                 "pipe_frac": FP64_PIPE_INST_PER_CELL[name] * wl.ncell / (per_launch_ms / 1e3) / 1e12 / peak_tinst,
                 "achieved_tflops": achieved_tflops, "peak_tflops": peak_tflops,
                 "frac_tflops": achieved_tflops / peak_tflops,
                 "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_src": peaks["src"],
                 "algorithmic_bytes_per_cell": HBM_BYTES_PER_CELL[name],
                 "jv_whole": {"fp64_inst_per_cell": sum(FP64_INST_PER_CELL[k] for k in JV_KERNELS),
+                             "int_pipe_ops_per_cell": sum(INT_PIPE_OPS_PER_CELL[k] for k in JV_KERNELS),
                              "achieved": jv_tinst, "frac": jv_tinst / peak_tinst if jv_tinst else None,
                              "ms_per_product": jv_ms / max(1, njv)}}
 

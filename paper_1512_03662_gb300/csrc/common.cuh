@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "emu64.cuh"
+
 namespace jfnk {
 
 constexpr int kBlock = 256;          // threads per block of the pointwise kernels
@@ -148,6 +152,75 @@ __device__ __forceinline__ double load_normal(const Grid& G, const double* __res
     return __longlong_as_double(__double_as_longlong(v) ^ flip);
 }
 
+// ---------------------------------------------------------------------------
+// Branch-free neighbour addressing of the residual kernels.  Offsets are flat
+// offsets relative to the thread's own cell (pointers given at that cell):
+// k * stride inside the grid; the periodic wrap or the wall mirror changes
+// them only where P + k e_d leaves the grid.  The boundary type is a kernel
+// parameter (uniform across the warp) and the position tests are selects,
+// so no thread-dependent branch splits a warp.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int grid_stride(const Grid& G, int d) {
+    return d == 0 ? 1 : (d == 1 ? G.n[0] : G.n[0] * G.n[1]);
+}
+
+// offset of the cell quantity at P + k e_d, 1 <= |k| <= 3 (k = 0: 0)
+__device__ __forceinline__ int cell_off(const Grid& G, const Idx3& P, int d, int k) {
+    const int i = P.i[d], n = G.n[d];
+    int m = k;
+    if (k < 0) {
+        // i + k < 0: periodic i + k + n, wall mirror -(i + k) - 1
+        const int w = G.bc[d] == 0 ? k + n : -2 * i - k - 1;
+        m = i + k < 0 ? w : k;
+    } else if (k > 0) {
+        // i + k >= n: periodic i + k - n, wall mirror 2n - 1 - (i + k)
+        const int w = G.bc[d] == 0 ? k - n : 2 * n - 1 - 2 * i - k;
+        m = i + k >= n ? w : k;
+    }
+    return m * grid_stride(G, d);
+}
+
+// velocity normal to direction c at face slot P + k e_c (uc at the thread's
+// own slot): with walls the odd mirror (sign flip on the integer pipe) and
+// zero on both wall faces; periodic faces wrap like cells
+__device__ __forceinline__ double normal_along(const Grid& G, const double* __restrict__ uc, const Idx3& P, int c,
+                                               int k) {
+    if (G.bc[c] == 0) return __ldg(uc + cell_off(G, P, c, k));
+    const int i = P.i[c], n = G.n[c], kk = i + k;
+    int m = k;
+    bool flip = false, zero = false;
+    if (k <= 0) zero = kk == 0;
+    if (k >= 0) zero = zero | (kk == n);
+    if (k < 0) {
+        flip = kk < 0;
+        m = flip ? -2 * i - k : k;                  // slot -kk
+    } else if (k > 0) {
+        flip = kk > n;
+        m = flip ? 2 * n - 2 * i - k : k;           // slot 2n - kk
+    }
+    const double v = __ldg(uc + (zero ? 0 : m) * grid_stride(G, c));   // the own slot where the value is zero
+    const long long f = flip ? (long long)0x8000000000000000ULL : 0ll;
+    return zero ? 0.0 : __longlong_as_double(__double_as_longlong(v) ^ f);
+}
+
+// velocity normal to direction c at slot P + k e_d, d != c (tangential
+// offsets map like cells); zero when the thread's own slot is a wall face
+// of c
+__device__ __forceinline__ double normal_across(const Grid& G, const double* __restrict__ uc, const Idx3& P, int c,
+                                                int d, int k) {
+    const bool wall = (G.bc[c] == 1) & (P.i[c] == 0);
+    const double v = __ldg(uc + cell_off(G, P, d, k));
+    return wall ? 0.0 : v;
+}
+
+// face quantity of direction d at the upper face of the cell (slot P + e_d):
+// zero at an upper wall
+__device__ __forceinline__ double face_up_at(const Grid& G, const double* __restrict__ f, const Idx3& P, int d) {
+    const bool top = (G.bc[d] == 1) & (P.i[d] + 1 == G.n[d]);
+    const double v = __ldg(f + (top ? 0 : cell_off(G, P, d, 1)));
+    return top ? 0.0 : v;
+}
+
 // True when slot p is the wall face of direction c.
 __device__ __forceinline__ bool is_wall_slot(const Grid& G, int c, const Idx3& p) {
     return G.bc[c] == 1 && p.i[c] == 0;
@@ -178,16 +251,57 @@ __device__ __forceinline__ bool positive(double x) { return __double_as_longlong
 // returned split as q + num/den: num = ab and den = a + b where the limiter
 // is on, num = 0 and den = 1 where it is off, so every thread divides (no
 // warp split) and a thread can form all its reciprocals together.
+// The arithmetic of one thread's evaluation, on the FP64 pipe (FpOps:
+// plain operators, which the compiler may fuse into FMAs) or on the integer
+// pipes (IntOps: emu64.cuh, the correctly rounded results of the unfused
+// operations, IM for the products and IA for the sums and differences).
+// The FP64 pipe of sm_103a issues one warp instruction per 64 cycles per
+// scheduler, so the FP64-bound kernels move part of their arithmetic to the
+// idle integer pipes.  IntOps collects one validity flag for the whole
+// sequence (operands and results normal or zero) instead of branching per
+// operation, so a kernel checks it once and redoes the thread's work with
+// FpOps where it failed; no branch splits the integer sequence, and the
+// compiler can interleave its independent chains.
+struct FpOps {
+    __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+    __device__ __forceinline__ void require(bool) {}
+    __device__ __forceinline__ bool valid() const { return true; }
+    static constexpr bool checked = false;
+};
+
+template <bool IM, bool IA>
+struct IntOps {
+    bool ok = true;
+    __device__ __forceinline__ double mul(double a, double b) {
+        if constexpr (IM) return emu::mul_chk(a, b, ok);
+        else return a * b;
+    }
+    __device__ __forceinline__ double add(double a, double b) {
+        if constexpr (IA) return emu::add_chk(a, b, ok);
+        else return a + b;
+    }
+    __device__ __forceinline__ double sub(double a, double b) {
+        if constexpr (IA) return emu::sub_chk(a, b, ok);
+        else return a - b;
+    }
+    __device__ __forceinline__ void require(bool c) { ok = ok & c; }
+    __device__ __forceinline__ bool valid() const { return ok; }
+    static constexpr bool checked = true;
+};
+
 struct Upw { double q, num, den; };
-__device__ __forceinline__ Upw upwind_parts(double q_near, double q_far, double q_other) {
-    const double a = q_near - q_far;
-    const double b = q_other - q_near;
-    const double ab = a * b;
+template <class O = FpOps>
+__device__ __forceinline__ Upw upwind_parts(double q_near, double q_far, double q_other, O&& ops = O()) {
+    const double a = ops.sub(q_near, q_far);
+    const double b = ops.sub(q_other, q_near);
+    const double ab = ops.mul(a, b);
     const bool on = positive(ab);
     Upw u;
     u.q = q_near;
     u.num = on ? ab : 0.0;
-    u.den = on ? a + b : 1.0;
+    u.den = on ? ops.add(a, b) : 1.0;
     return u;
 }
 
@@ -281,8 +395,10 @@ __device__ __forceinline__ double recip_nr(double d) {
 // normal range when every |d_i| lies in [2^-R, 2^R), R = 1000/K (exponent
 // test on the high word, integer pipe); otherwise the thread divides K
 // times.
-template <int K>
-__device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K]) {
+// With checked Ops (IntOps) the range test goes into its flag and there is
+// no division fallback: the caller redoes the whole evaluation.
+template <int K, class O = FpOps>
+__device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K], O&& ops = O()) {
     constexpr unsigned R = 1000u / K;
     bool ok = true;
 #pragma unroll
@@ -290,16 +406,17 @@ __device__ __forceinline__ void recip_all(const double (&d)[K], double (&r)[K]) 
         const unsigned e = ((unsigned)__double2hiint(d[i]) >> 20) & 0x7ffu;
         ok = ok & (e - (1023u - R) < 2u * R);
     }
-    if (ok) {
+    if constexpr (std::remove_reference_t<O>::checked) ops.require(ok);
+    if (std::remove_reference_t<O>::checked || ok) {
         double p[K];
         p[0] = d[0];
 #pragma unroll
-        for (int i = 1; i < K; ++i) p[i] = p[i - 1] * d[i];
+        for (int i = 1; i < K; ++i) p[i] = ops.mul(p[i - 1], d[i]);
         double inv = recip_nr(p[K - 1]);
 #pragma unroll
         for (int i = K - 1; i > 0; --i) {
-            r[i] = inv * p[i - 1];
-            inv = inv * d[i];
+            r[i] = ops.mul(inv, p[i - 1]);
+            inv = ops.mul(inv, d[i]);
         }
         r[0] = inv;
     } else {

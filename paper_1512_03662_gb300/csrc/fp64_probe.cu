@@ -2,7 +2,9 @@
 // kernels are compared against; and checks, run by the tests, of device
 // functions of the solver's kernels: the Newton-Raphson reciprocal
 // (recip_nr) against IEEE division, and the integer-pipe float/double
-// conversions (f2d_exact, d2f_rn) against the conversion instructions.
+// conversions (f2d_exact, d2f_rn) against the conversion instructions,
+// and the integer-pipe products and sums (emu::mul_rn, emu::add_rn,
+// emu::sub_rn) against the DMUL / DADD instructions.
 //
 // Every thread runs eight independent chains of fused multiply-adds
 // x <- x * a + b (one DFMA instruction, two flops each), so the FP64 pipe
@@ -14,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "emu64.cuh"
 
 namespace {
 
@@ -47,6 +50,16 @@ __global__ void k_conv_check(const double* __restrict__ x, const float* __restri
     }
 }
 
+__global__ void k_emu_check(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ m,
+                            double* __restrict__ s, double* __restrict__ d, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) {
+        m[i] = jfnk::emu::mul_rn(a[i], b[i]);
+        s[i] = jfnk::emu::add_rn(a[i], b[i]);
+        d[i] = jfnk::emu::sub_rn(a[i], b[i]);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -69,6 +82,17 @@ int fp64_recip_check(const double* d, double* r, long long n, void* stream) {
     const long long blocks = (n + 255) / 256;
     if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
     k_recip_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
+    return (int)cudaGetLastError();
+}
+
+// m[i] = a[i] * b[i], s[i] = a[i] + b[i], d[i] = a[i] - b[i] on the integer
+// pipes (emu64.cuh) for i < n, queued on `stream`; all device arrays of n
+// doubles.
+int fp64_emu_check(const double* a, const double* b, double* m, double* s, double* d, long long n, void* stream) {
+    if (!a || !b || !m || !s || !d || n <= 0) return (int)cudaErrorInvalidValue;
+    const long long blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    k_emu_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, m, s, d, n);
     return (int)cudaGetLastError();
 }
 

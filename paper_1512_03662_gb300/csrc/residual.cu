@@ -7,7 +7,11 @@
 //
 // The evaluation is split so that every van Leer slope and every flux is
 // computed once per slot (the FP64 rate of sm_103a, about 0.6 TFMA/s, binds
-// these kernels, not HBM):
+// these kernels, not HBM).  The flux kernels form their products on the
+// integer pipes (emu64.cuh: the same correctly rounded bits, checked once per
+// evaluation, redone on the FP64 pipe where an operand left the normal
+// range) and address neighbours with branch-free offsets (common.cuh), so
+// the FP64 pipe keeps the sums and the fused multiply-adds only:
 //   k_eos          p, T per cell (perturbed state written first by k_perturb)
 //   k_face_fluxes  mass flux Fm_d and energy flux FE_d (advective part minus
 //                  conduction) on the lower face of every cell, per direction
@@ -61,11 +65,9 @@ __global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__
         double ke = 0.0;
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            const double* u = X + (2 + d) * nc;
-            int o[3] = {0, 0, 0};
-            o[d] = 1;
-            double ul = load_normal(G, u, d, P, 0, 0, 0);
-            double uu = load_normal(G, u, d, P, o[0], o[1], o[2]);
+            const double* u = X + (2 + d) * nc + c;
+            const double ul = normal_along(G, u, P, d, 0);
+            const double uu = normal_along(G, u, P, d, 1);
             ke = ke + 0.25 * (ul * ul + uu * uu);
         }
         e = e - ke;
@@ -76,135 +78,246 @@ __global__ void k_eos(Grid G, const double* __restrict__ X, double* __restrict__
     if (G.has_cond) chi[c] = conductivity(G, Tc);
 }
 
-template <int ND>
-__global__ void k_face_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ p,
+// Mass and energy flux of the lower face of direction d of one cell (its
+// own reciprocal batch of two); with checked Ops nothing is written unless
+// every operation was in range.
+template <int ND, int EF, class O>
+__device__ __forceinline__ bool face_flux_dir(O ops, const Grid& G, const double* __restrict__ X,
+                                              const double* __restrict__ p, const double* __restrict__ T,
+                                              const double* __restrict__ chi, double* __restrict__ Fm,
+                                              double* __restrict__ FE, int d, const Idx3& P, long long c) {
+    const long long nc = G.ncell;
+    const double* rho = X + c;
+    const double* E = X + nc + c;
+    const double u = normal_along(G, X + (2 + d) * nc + c, P, d, 0);
+    const int om2 = cell_off(G, P, d, -2), om1 = cell_off(G, P, d, -1), op1 = cell_off(G, P, d, 1);
+    const double r0 = __ldg(rho), e0 = __ldg(E);
+    const double r2 = __ldg(rho + om2), e2 = __ldg(E + om2);
+    const double r1 = __ldg(rho + om1), e1 = __ldg(E + om1);
+    const double r3 = __ldg(rho + op1), e3 = __ldg(E + op1);
+    // upwind side: cell i-1 for u >= 0 (ties to the lower side), else cell i
+    const bool left = nonneg(u);
+    const Upw ur = upwind_parts(left ? r1 : r0, left ? r2 : r3, left ? r0 : r1, ops);
+    const Upw ue = upwind_parts(left ? e1 : e0, left ? e2 : e3, left ? e0 : e1, ops);
+    // one reciprocal for the two limited slopes
+    double den[2] = {ur.den, ue.den}, inv[2];
+    recip_all<2>(den, inv, ops);
+    const double fm = ops.mul(u, fma(ur.num, inv[0], ur.q));
+    double fe = ops.mul(fm, fma(ue.num, inv[1], ue.q));
+    if constexpr (EF == 1) {
+        const double pl = __ldg(p + c + om1);
+        fe = fe + 0.5 * (pl + __ldg(p + c)) * u;
+    }
+    if (G.has_cond) {
+        // q = chi_f (T_c - T_l) / dx with chi_f the mean of the two cells
+        const double Tl = __ldg(T + c + om1);
+        const double chil = __ldg(chi + c + om1);
+        const double sq = ops.mul(chil + __ldg(chi + c), G.hidx[d]);
+        fe = fma(-sq, __ldg(T + c) - Tl, fe);
+    }
+    if (!ops.valid()) return false;
+    Fm[d * nc + c] = fm;                  // mass flux (every consumer takes half the sum of two)
+    FE[d * nc + c] = fe;
+    return true;
+}
+
+// products of the face fluxes on the integer pipes, sums on the FP64 pipe
+using FaceOps = IntOps<true, false>;
+
+// the FP64-pipe redo of one direction, out of line: inlined, the compiler
+// predicates part of it into the fast path, where its FP64 instructions
+// still occupy the FP64 pipe with every lane switched off
+template <int ND, int EF>
+__device__ __noinline__ void face_flux_dir_fp64(const Grid G, const double* __restrict__ X,
+                                                const double* __restrict__ p, const double* __restrict__ T,
+                                                const double* __restrict__ chi, double* __restrict__ Fm,
+                                                double* __restrict__ FE, int d, const Idx3 P, long long c) {
+    face_flux_dir<ND, EF>(FpOps(), G, X, p, T, chi, Fm, FE, d, P, c);
+}
+
+// one direction at a time (a reciprocal batch of two instead of 2 ND keeps
+// the live state small); at least 6 blocks of 128 threads per SM: 80
+// registers.  The energy form EF (0: internal, 1: total) is a template
+// parameter: as a runtime test its pressure-work term was predicated, and
+// its FP64 instructions occupied the FP64 pipe with every lane off.
+template <int ND, int EF>
+__global__ void __launch_bounds__(128, 6) k_face_fluxes(Grid G, const double* __restrict__ X, const double* __restrict__ p,
                               const double* __restrict__ T, const double* __restrict__ chi, double* __restrict__ Fm,
                               double* __restrict__ FE) {
     Idx3 P;
     long long c;
     if (!cell_pos(G.n, P, c)) return;
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+        if (!face_flux_dir<ND, EF>(FaceOps(), G, X, p, T, chi, Fm, FE, d, P, c))
+            face_flux_dir_fp64<ND, EF>(G, X, p, T, chi, Fm, FE, d, P, c);
+}
+
+// Momentum fluxes Psi_cd (d = 0..ND-1) of component c at one cell; with
+// checked Ops nothing is written unless every operation was in range.
+template <int ND, class O>
+__device__ __forceinline__ bool mom_fluxes_component(O ops, const Grid& G, const double* __restrict__ X,
+                                                     const double* __restrict__ Fm, double* __restrict__ Psi,
+                                                     int c, const Idx3& P, long long cc) {
     const long long nc = G.ncell;
-    const double* rho = X;
-    const double* E = X + nc;
-    const double r0 = __ldg(rho + c), e0 = __ldg(E + c);
-    // pass 1: loads and the split upwind values of rho and E on every face
-    double u[ND];
-    Upw up[2 * ND];
+    constexpr int nd = ND;
+    const double* uc = X + (2 + c) * nc + cc;         // pointers at the thread's own slot
+    // pass 1: loads, carrying mass flux and split upwind value
+    double mf[nd];
+    Upw up[nd];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        int o[3] = {0, 0, 0};
-        u[d] = load_normal(G, X + (2 + d) * nc, d, P, 0, 0, 0);
-        o[d] = -2; const double r2 = load_cell(G, rho, P, o[0], o[1], o[2]), e2 = load_cell(G, E, P, o[0], o[1], o[2]);
-        o[d] = -1; const double r1 = load_cell(G, rho, P, o[0], o[1], o[2]), e1 = load_cell(G, E, P, o[0], o[1], o[2]);
-        o[d] = 1;  const double r3 = load_cell(G, rho, P, o[0], o[1], o[2]), e3 = load_cell(G, E, P, o[0], o[1], o[2]);
-        // upwind side: cell i-1 for u >= 0 (ties to the lower side), else cell i
-        const bool left = nonneg(u[d]);
-        up[2 * d] = upwind_parts(left ? r1 : r0, left ? r2 : r3, left ? r0 : r1);
-        up[2 * d + 1] = upwind_parts(left ? e1 : e0, left ? e2 : e3, left ? e0 : e1);
-    }
-    // pass 2: one division for all limited slopes of the cell
-    double den[2 * ND], inv[2 * ND];
-#pragma unroll
-    for (int k = 0; k < 2 * ND; ++k) den[k] = up[k].den;
-    recip_all<2 * ND>(den, inv);
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        int o[3] = {0, 0, 0};
-        const double rho_up = up[2 * d].q + up[2 * d].num * inv[2 * d];
-        const double E_up = up[2 * d + 1].q + up[2 * d + 1].num * inv[2 * d + 1];
-        double fm = u[d] * rho_up;
-        double fe = fm * E_up;
-        o[d] = -1;
-        if (G.energy_form == 1) {
-            double pl = load_cell(G, p, P, o[0], o[1], o[2]);
-            fe = fe + 0.5 * (pl + __ldg(p + c)) * u[d];
+    for (int d = 0; d < nd; ++d) {
+        double m, q_near, q_far, q_other;
+        const double* fmd = Fm + d * nc + cc;
+        if (c == d) {
+            // flux at the cell centre between faces i and i+1 along c, carried
+            // by the mean of the two mass fluxes (here their sum: Psi doubled)
+            m = __ldg(fmd) + face_up_at(G, fmd, P, c);
+            const double um = normal_along(G, uc, P, c, -1);
+            const double u0 = normal_along(G, uc, P, c, 0);
+            const double u1 = normal_along(G, uc, P, c, 1);
+            const double u2 = normal_along(G, uc, P, c, 2);
+            const bool left = nonneg(m);
+            q_near = left ? u0 : u1;
+            q_far = left ? um : u2;
+            q_other = left ? u1 : u0;
+        } else {
+            // flux on the edge between c-face i_c and d-face i_d
+            m = __ldg(fmd + cell_off(G, P, c, -1)) + __ldg(fmd);
+            const double u2 = normal_across(G, uc, P, c, d, -2);
+            const double u1 = normal_across(G, uc, P, c, d, -1);
+            const double u0 = normal_across(G, uc, P, c, d, 0);
+            const double u3 = normal_across(G, uc, P, c, d, 1);
+            const bool left = nonneg(m);
+            q_near = left ? u1 : u0;
+            q_far = left ? u2 : u3;
+            q_other = left ? u0 : u1;
         }
-        if (G.has_cond) {
-            // q = chi_f (T_c - T_l) / dx with chi_f the mean of the two cells
-            const double Tl = load_cell(G, T, P, o[0], o[1], o[2]);
-            const double chil = load_cell(G, chi, P, o[0], o[1], o[2]);
-            const double sq = (chil + __ldg(chi + c)) * G.hidx[d];
-            fe = fma(-sq, __ldg(T + c) - Tl, fe);
-        }
-        Fm[d * nc + c] = fm;                  // mass flux (every consumer takes half the sum of two)
-        FE[d * nc + c] = fe;
+        mf[d] = m;
+        up[d] = upwind_parts(q_near, q_far, q_other, ops);
     }
+    // pass 2: one division for the nd limited slopes of component c (a
+    // batch of nd keeps the kernel near 56 registers; one batch of nd^2
+    // needed 102 and ran 20 % slower at the lower occupancy)
+    double den[nd], inv[nd], psi[nd];
+#pragma unroll
+    for (int d = 0; d < nd; ++d) den[d] = up[d].den;
+    recip_all<nd>(den, inv, ops);
+#pragma unroll
+    for (int d = 0; d < nd; ++d) psi[d] = ops.mul(mf[d], fma(up[d].num, inv[d], up[d].q));
+    if (!ops.valid()) return false;
+#pragma unroll
+    for (int d = 0; d < nd; ++d) Psi[(c * nd + d) * nc + cc] = psi[d];
+    return true;
 }
 
-// Fm_d at slot (pos + off) where the offset is along a direction in which Fm_d
-// behaves as a cell quantity (any direction other than d).
-__device__ __forceinline__ double load_Fm_cell(const Grid& G, const double* Fm_d, const Idx3& P, int o0, int o1, int o2) {
-    return load_cell(G, Fm_d, P, o0, o1, o2);
+// products of the momentum fluxes on the integer pipes, sums on the FP64 pipe
+using MomOps = IntOps<true, false>;
+
+// the FP64-pipe redo of one component, out of line (see face_flux_dir_fp64)
+template <int ND>
+__device__ __noinline__ void mom_fluxes_component_fp64(const Grid G, const double* __restrict__ X,
+                                                       const double* __restrict__ Fm, double* __restrict__ Psi,
+                                                       int c, const Idx3 P, long long cc) {
+    mom_fluxes_component<ND>(FpOps(), G, X, Fm, Psi, c, P, cc);
 }
 
-// Fm_d at the upper face (slot + 1 along d): zero at an upper wall.
-__device__ __forceinline__ double load_face_up(const Grid& G, const double* f, int d, const Idx3& P) {
-    if (G.bc[d] == 1 && P.i[d] + 1 == G.n[d]) return 0.0;
-    int o[3] = {0, 0, 0};
-    o[d] = 1;
-    return load_cell(G, f, P, o[0], o[1], o[2]);
-}
-
-// 128-thread blocks, at least 10 resident per SM: 48 registers (no spills)
-// instead of 54, 40 warps per SM instead of 36
+// 128-thread blocks, at least 10 resident per SM (48 registers); the
+// components run as a loop (not unrolled), which keeps the straight-line
+// code, and the instruction-cache misses of its warps, three times smaller
 template <int ND>
 __global__ void __launch_bounds__(128, 10) k_mom_fluxes(Grid G, const double* __restrict__ X,
                                                         const double* __restrict__ Fm, double* __restrict__ Psi) {
     Idx3 P;
     long long cc;
     if (!cell_pos(G.n, P, cc)) return;
+#pragma unroll 1
+    for (int c = 0; c < ND; ++c)
+        if (!mom_fluxes_component<ND>(MomOps(), G, X, Fm, Psi, c, P, cc))
+            mom_fluxes_component_fp64<ND>(G, X, Fm, Psi, c, P, cc);
+}
+
+// Divergences and sources Rv and conserved variables Uv of one cell, the
+// products on the integer pipes with checked Ops (false, nothing valid,
+// where one was out of range)
+template <int ND, class O>
+__device__ __forceinline__ bool assemble_terms(O ops, const Grid& G, const double* __restrict__ X,
+                                               const double* __restrict__ p, const double* __restrict__ Fm,
+                                               const double* __restrict__ FE, const double* __restrict__ Psi,
+                                               const Idx3& P, long long cc, double (&Uv)[2 + ND],
+                                               double (&Rv)[2 + ND]) {
     const long long nc = G.ncell;
     constexpr int nd = ND;
-    // pass 1 per component c: loads, carrying mass flux and split upwind value
-    double mf[nd * nd];
-    Upw up[nd * nd];
+    double Rr = 0.0, RE = 0.0, divu = 0.0;
+#pragma unroll
+    for (int d = 0; d < nd; ++d) {
+        const double* fmd = Fm + d * nc + cc;              // pointers at the thread's own cell
+        const double* fed = FE + d * nc + cc;
+        const double fm0 = __ldg(fmd), fm1 = face_up_at(G, fmd, P, d);
+        const double fe0 = __ldg(fed), fe1 = face_up_at(G, fed, P, d);
+        Rr = Rr - (fm1 - fm0) * G.idx[d];
+        RE = RE - (fe1 - fe0) * G.idx[d];
+        if (G.energy_form == 0) {
+            const double* ud = X + (2 + d) * nc + cc;
+            const double u0 = normal_along(G, ud, P, d, 0);
+            const double u1 = normal_along(G, ud, P, d, 1);
+            divu = divu + (u1 - u0) * G.idx[d];
+        } else if ((G.gmask >> d) & 1) {
+            RE = RE + G.hg[d] * (fm0 + fm1);
+        }
+    }
+    const double pc = __ldg(p + cc);
+    if (G.energy_form == 0) RE = RE - pc * divu;
+
+    const double rho = __ldg(X + cc);
+    Uv[0] = rho;            Rv[0] = Rr;
+    Uv[1] = ops.mul(rho, __ldg(X + nc + cc)); Rv[1] = RE;
 #pragma unroll
     for (int c = 0; c < nd; ++c) {
-        const double* uc = X + (2 + c) * nc;
+        // every thread evaluates (wall slots read mirrored, in-range cells)
+        // and wall slots select zero, so no branch splits the warp
+        const int om1 = cell_off(G, P, c, -1);
+        const double pl = __ldg(p + cc + om1);
+        const double rl = __ldg(X + cc + om1);
+        // rs = rl + rho = 2 rho_f: the 1/2 of the face mean is carried by
+        // g/2 here and by the halved 1/dt factors of the momentum rows below
+        // (exact powers of two: the results are those of rho_f itself)
+        const double rs = rl + rho;
+        double Rc = ops.mul(pl - pc, G.idx[c]);
+        if ((G.gmask >> c) & 1) Rc = fma(rs, G.hg[c], Rc);
 #pragma unroll
         for (int d = 0; d < nd; ++d) {
-            double m, q_near, q_far, q_other;
-            int o[3] = {0, 0, 0};
+            const double* ps = Psi + (c * nd + d) * nc + cc;
+            double a, b;
             if (c == d) {
-                // flux at the cell centre between faces i and i+1 along c, carried
-                // by the mean of the two mass fluxes (here their sum: Psi doubled)
-                m = __ldg(Fm + c * nc + cc) + load_face_up(G, Fm + c * nc, c, P);
-                o[c] = -1; const double um = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
-                o[c] = 1;  const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                o[c] = 2;  const double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                const bool left = nonneg(m);
-                q_near = left ? u0 : u1;
-                q_far = left ? um : u2;
-                q_other = left ? u1 : u0;
+                b = __ldg(ps);
+                a = __ldg(ps + om1);                          // centre i-1 along c
+                Rc = Rc - (b - a) * G.hidx[c];         // Psi stored doubled
             } else {
-                // flux on the edge between c-face i_c and d-face i_d
-                o[c] = -1;
-                m = load_Fm_cell(G, Fm + d * nc, P, o[0], o[1], o[2]) + __ldg(Fm + d * nc + cc);
-                o[c] = 0;
-                o[d] = -2; const double u2 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                o[d] = -1; const double u1 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                const double u0 = load_normal(G, uc, c, P, 0, 0, 0);
-                o[d] = 1;  const double u3 = load_normal(G, uc, c, P, o[0], o[1], o[2]);
-                const bool left = nonneg(m);
-                q_near = left ? u1 : u0;
-                q_far = left ? u2 : u3;
-                q_other = left ? u0 : u1;
+                a = __ldg(ps);
+                b = face_up_at(G, ps, P, d);
+                Rc = Rc - (b - a) * G.hidx[d];
             }
-            mf[c * nd + d] = m;
-            up[c * nd + d] = upwind_parts(q_near, q_far, q_other);
         }
-        // pass 2: one division for the nd limited slopes of component c (a
-        // batch of nd keeps the kernel near 56 registers; one batch of nd^2
-        // needed 102 and ran 20 % slower at the lower occupancy)
-        double den[nd], inv[nd];
-#pragma unroll
-        for (int d = 0; d < nd; ++d) den[d] = up[c * nd + d].den;
-        recip_all<nd>(den, inv);
-#pragma unroll
-        for (int d = 0; d < nd; ++d)
-            Psi[(c * nd + d) * nc + cc] = mf[c * nd + d] * (up[c * nd + d].q + up[c * nd + d].num * inv[d]);
+        const bool wall = is_wall_slot(G, c, P);
+        Uv[2 + c] = wall ? 0.0 : ops.mul(rs, __ldg(X + (2 + c) * nc + cc));        // 2 rho_f u
+        Rv[2 + c] = wall ? 0.0 : Rc;
     }
+    return ops.valid();
+}
+
+template <int ND> struct AsmTerms { double U[2 + ND], R[2 + ND]; };
+
+// the FP64-pipe redo, out of line (see face_flux_dir_fp64); the terms come
+// back by value so that the caller's arrays stay in registers
+template <int ND>
+__device__ __noinline__ AsmTerms<ND> assemble_terms_fp64(const Grid G, const double* __restrict__ X,
+                                                         const double* __restrict__ p, const double* __restrict__ Fm,
+                                                         const double* __restrict__ FE,
+                                                         const double* __restrict__ Psi, const Idx3 P, long long cc) {
+    AsmTerms<ND> t;
+    assemble_terms<ND>(FpOps(), G, X, p, Fm, FE, Psi, P, cc, t.U, t.R);
+    return t;
 }
 
 template <int ND, int MODE, typename TO>
@@ -223,62 +336,14 @@ __global__ void k_assemble(Grid G, const double* __restrict__ X, const double* _
     double inv_delta = 0.0;
     if (MODE == kModeJv) inv_delta = scal[kSlotInvDelta];
 
-    double Rr = 0.0, RE = 0.0, divu = 0.0;
-#pragma unroll
-    for (int d = 0; d < nd; ++d) {
-        const double* fmd = Fm + d * nc;
-        const double* fed = FE + d * nc;
-        double fm0 = __ldg(fmd + cc), fm1 = load_face_up(G, fmd, d, P);
-        double fe0 = __ldg(fed + cc), fe1 = load_face_up(G, fed, d, P);
-        Rr = Rr - (fm1 - fm0) * G.idx[d];
-        RE = RE - (fe1 - fe0) * G.idx[d];
-        if (G.energy_form == 0) {
-            const double* ud = X + (2 + d) * nc;
-            double u0 = load_normal(G, ud, d, P, 0, 0, 0);
-            int o[3] = {0, 0, 0};
-            o[d] = 1;
-            double u1 = load_normal(G, ud, d, P, o[0], o[1], o[2]);
-            divu = divu + (u1 - u0) * G.idx[d];
-        } else if ((G.gmask >> d) & 1) {
-            RE = RE + G.hg[d] * (fm0 + fm1);
-        }
-    }
-    const double pc = __ldg(p + cc);
-    if (G.energy_form == 0) RE = RE - pc * divu;
-
-    const double rho = __ldg(X + cc);
     double Uv[2 + ND], Rv[2 + ND];
-    Uv[0] = rho;            Rv[0] = Rr;
-    Uv[1] = rho * __ldg(X + nc + cc); Rv[1] = RE;
+    if (!assemble_terms<ND>(IntOps<true, false>(), G, X, p, Fm, FE, Psi, P, cc, Uv, Rv)) {
+        const AsmTerms<ND> t = assemble_terms_fp64<ND>(G, X, p, Fm, FE, Psi, P, cc);
 #pragma unroll
-    for (int c = 0; c < nd; ++c) {
-        if (is_wall_slot(G, c, P)) { Uv[2 + c] = 0.0; Rv[2 + c] = 0.0; continue; }
-        int o[3] = {0, 0, 0};
-        o[c] = -1;
-        double pl = load_cell(G, p, P, o[0], o[1], o[2]);
-        double rl = load_cell(G, X, P, o[0], o[1], o[2]);
-        // rs = rl + rho = 2 rho_f: the 1/2 of the face mean is carried by
-        // g/2 here and by the halved 1/dt factors of the momentum rows below
-        // (exact powers of two: the results are those of rho_f itself)
-        const double rs = rl + rho;
-        double Rc = -(pc - pl) * G.idx[c];
-        if ((G.gmask >> c) & 1) Rc = fma(rs, G.hg[c], Rc);
-#pragma unroll
-        for (int d = 0; d < nd; ++d) {
-            const double* ps = Psi + (c * nd + d) * nc;
-            double a, b;
-            if (c == d) {
-                b = __ldg(ps + cc);
-                a = load_cell(G, ps, P, o[0], o[1], o[2]);      // centre i-1 along c
-                Rc = Rc - (b - a) * G.hidx[c];              // Psi stored doubled
-            } else {
-                a = __ldg(ps + cc);
-                b = load_face_up(G, ps, d, P);
-                Rc = Rc - (b - a) * G.hidx[d];
-            }
+        for (int k = 0; k < 2 + ND; ++k) {
+            Uv[k] = t.U[k];
+            Rv[k] = t.R[k];
         }
-        Uv[2 + c] = rs * __ldg(X + (2 + c) * nc + cc);        // 2 rho_f u
-        Rv[2 + c] = Rc;
     }
 #pragma unroll
     for (int k = 0; k < 2 + nd; ++k) {
@@ -445,7 +510,15 @@ template void launch_perturb<float>(const Grid&, const double*, const float*, co
 
 void launch_face_fluxes(const Grid& G, const double* X, const double* p, const double* T, const double* chi,
                         double* Fm, double* FE, cudaStream_t s) {
-    CELL_LAUNCH(k_face_fluxes, G, X, p, T, chi, Fm, FE);
+    const CellLaunch cl = cell_launch(G.n);
+    ++g_launch_count;
+    if (G.ndim == 3) {
+        if (G.energy_form == 1) k_face_fluxes<3, 1><<<cl.grid, cl.block, 0, s>>>(G, X, p, T, chi, Fm, FE);
+        else k_face_fluxes<3, 0><<<cl.grid, cl.block, 0, s>>>(G, X, p, T, chi, Fm, FE);
+    } else {
+        if (G.energy_form == 1) k_face_fluxes<2, 1><<<cl.grid, cl.block, 0, s>>>(G, X, p, T, chi, Fm, FE);
+        else k_face_fluxes<2, 0><<<cl.grid, cl.block, 0, s>>>(G, X, p, T, chi, Fm, FE);
+    }
 }
 
 void launch_mom_fluxes(const Grid& G, const double* X, const double* Fm, double* Psi, cudaStream_t s) {

@@ -9,6 +9,8 @@ import numpy as np
 import pytest
 import torch
 
+from emu_cases import emu_operands
+
 pytestmark = pytest.mark.gpu
 
 
@@ -103,3 +105,26 @@ def test_integer_pipe_conversions_equal_the_conversion_instructions(probe):
     same_d = (fd.view(torch.int64) == ref_d.view(torch.int64)) | (torch.isnan(fd) & torch.isnan(ref_d))
     assert bool(same_f.all()), x[~same_f.cpu().numpy()][:8]
     assert bool(same_d.all()), f[~same_d.cpu().numpy()][:8]
+
+
+def test_integer_pipe_products_and_sums_equal_dmul_dadd(probe):
+    """emu::mul_rn, add_rn and sub_rn (the products and sums the flux
+    kernels move off the FP64 pipe) give the bits of the DMUL / DADD
+    instructions, computed by torch on the same device, for every class of
+    input; NaN stays NaN."""
+    probe.fp64_emu_check.restype = ctypes.c_int
+    probe.fp64_emu_check.argtypes = [ctypes.c_void_p] * 5 + [ctypes.c_longlong, ctypes.c_void_p]
+    n = 1 << 23
+    a, b = emu_operands(n, 17)
+    ag = torch.as_tensor(a, device="cuda")
+    bg = torch.as_tensor(b, device="cuda")
+    m = torch.empty_like(ag)
+    s = torch.empty_like(ag)
+    d = torch.empty_like(ag)
+    assert probe.fp64_emu_check(*(ctypes.c_void_p(t.data_ptr()) for t in (ag, bg, m, s, d)), n, None) == 0
+    refs = (ag * bg, ag + bg, ag - bg)
+    torch.cuda.synchronize()
+    for name, got, ref in zip(("mul", "add", "sub"), (m, s, d), refs):
+        same = (got.view(torch.int64) == ref.view(torch.int64)) | (torch.isnan(got) & torch.isnan(ref))
+        bad = (~same).nonzero().flatten()[:4].cpu().numpy()
+        assert bool(same.all()), (name, a[bad], b[bad], got.cpu().numpy()[bad], ref.cpu().numpy()[bad])
