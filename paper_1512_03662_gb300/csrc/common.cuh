@@ -235,11 +235,18 @@ __device__ __forceinline__ double vanleer(double a, double b) {
 // Sign tests on the bit pattern (integer pipe; the flux kernels are bound by
 // the FP64 pipe).  For every non-NaN x: nonneg(x) == (x >= 0.0) (both zeros
 // count), positive(x) == (x > 0.0).
+// Both on the two 32-bit words: as 64-bit tests of the whole pattern the
+// compiler turned nonneg into an FP64 compare (DSETP) on the FP64 pipe.
 __device__ __forceinline__ bool nonneg(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b >> 63) == 0ull || (b << 1) == 0ull;
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    return (hi >= 0) | ((((unsigned)hi << 1) | lo) == 0u);
 }
-__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    return (hi > 0) | ((hi == 0) & (lo != 0u));
+}
 
 // Upwind reconstruction without divergent branches.  With q_near the cell
 // on the upwind side of the face, q_far its other neighbour and q_other the
