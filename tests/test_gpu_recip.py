@@ -1,5 +1,6 @@
 """The reciprocal of the batched inversion in the flux kernels (recip_nr:
-rcp.approx.ftz.f64 refined by two Newton-Raphson steps, Markstein 1990)
+rcp.approx.ftz.f64 refined by one third-order step of the reciprocal
+iteration, Markstein 1990)
 against CUDA's IEEE division 1.0 / d on the device: at most one unit in the
 last place apart over the exponent range the kernels allow (|d| in
 [2^-1000, 2^1000), where the inversion takes this path), mostly equal."""
