@@ -400,8 +400,74 @@ __device__ __forceinline__ double internal_e(const Grid& G, const double* X, con
     return E - ke;
 }
 
+// L, R, their inverses and the squares of x_hat = R^-1 X of one cell; the
+// products of the batched inversion on the integer pipes with checked Ops
+// (nothing written, false, where one was out of range)
+template <int ND, class O>
+__device__ __forceinline__ bool scaling_cell(O ops, const Grid& G, const double* __restrict__ X, double alpha1,
+                                             double alpha2, double* __restrict__ L, double* __restrict__ R,
+                                             double* __restrict__ Linv, double* __restrict__ Rinv, const Idx3& P,
+                                             long long cc, double& acc) {
+    const long long nc = G.ncell;
+    double rho = X[cc], E = X[nc + cc];
+    double Lv[2 + ND], Rv[2 + ND];
+    Lv[0] = rho; Rv[0] = rho;
+    Lv[1] = rho * E; Rv[1] = E;
+    double e0 = internal_e(G, X, P, 0, 0, 0);
+    double cs0 = sqrt(G.gamma * G.gm1 * e0);
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+        if (is_wall_slot(G, c, P)) { Lv[2 + c] = 1.0; Rv[2 + c] = 1.0; continue; }
+        int o[3] = {0, 0, 0};
+        o[c] = -1;
+        double rl = load_cell(G, X, P, o[0], o[1], o[2]);
+        double el = internal_e(G, X, P, o[0], o[1], o[2]);
+        double csl = sqrt(G.gamma * G.gm1 * el);
+        double rho_f = 0.5 * (rl + rho);
+        double cs_f = 0.5 * (csl + cs0);
+        double au = fabs(X[(2 + c) * nc + cc]);
+        Lv[2 + c] = rho_f * fmax(au, alpha1 * cs_f);
+        Rv[2 + c] = fmax(au, alpha2 * cs_f);
+    }
+    // all 2(2+ND) reciprocals with one division
+    double den[2 * (2 + ND)], inv[2 * (2 + ND)];
+#pragma unroll
+    for (int k = 0; k < 2 + ND; ++k) {
+        den[k] = Lv[k];
+        den[2 + ND + k] = Rv[k];
+    }
+    recip_all<2 * (2 + ND)>(den, inv, ops);
+    if (!ops.valid()) return false;
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2 + ND; ++k) {
+        long long j = k * nc + cc;
+        L[j] = Lv[k];
+        R[j] = Rv[k];
+        Linv[j] = inv[k];
+        Rinv[j] = inv[2 + ND + k];
+        double xh = X[j] * inv[2 + ND + k];
+        if (k >= 2 && is_wall_slot(G, k - 2, P)) xh = 0.0;
+        a += xh * xh;
+    }
+    acc = a;
+    return true;
+}
+
 template <int ND>
-__global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, double alpha2,
+__device__ __noinline__ double scaling_cell_fp64(const Grid G, const double* __restrict__ X, double alpha1,
+                                                 double alpha2, double* __restrict__ L, double* __restrict__ R,
+                                                 double* __restrict__ Linv, double* __restrict__ Rinv, const Idx3 P,
+                                                 long long cc) {
+    double acc = 0.0;
+    scaling_cell<ND>(FpOps(), G, X, alpha1, alpha2, L, R, Linv, Rinv, P, cc, acc);
+    return acc;
+}
+
+// at least 6 blocks of 128 threads per SM (80 registers; 126 without the
+// bound ran slower)
+template <int ND>
+__global__ void __launch_bounds__(128, 6) k_scaling(Grid G, const double* __restrict__ X, double alpha1, double alpha2,
                           double* __restrict__ L, double* __restrict__ R, double* __restrict__ Linv,
                           double* __restrict__ Rinv, double* __restrict__ partials) {
     __shared__ double sh[32];
@@ -409,46 +475,8 @@ __global__ void k_scaling(Grid G, const double* __restrict__ X, double alpha1, d
     long long cc;
     double acc = 0.0;
     if (cell_pos(G.n, P, cc)) {
-        const long long nc = G.ncell;
-        double rho = X[cc], E = X[nc + cc];
-        double Lv[2 + ND], Rv[2 + ND];
-        Lv[0] = rho; Rv[0] = rho;
-        Lv[1] = rho * E; Rv[1] = E;
-        double e0 = internal_e(G, X, P, 0, 0, 0);
-        double cs0 = sqrt(G.gamma * G.gm1 * e0);
-#pragma unroll
-        for (int c = 0; c < ND; ++c) {
-            if (is_wall_slot(G, c, P)) { Lv[2 + c] = 1.0; Rv[2 + c] = 1.0; continue; }
-            int o[3] = {0, 0, 0};
-            o[c] = -1;
-            double rl = load_cell(G, X, P, o[0], o[1], o[2]);
-            double el = internal_e(G, X, P, o[0], o[1], o[2]);
-            double csl = sqrt(G.gamma * G.gm1 * el);
-            double rho_f = 0.5 * (rl + rho);
-            double cs_f = 0.5 * (csl + cs0);
-            double au = fabs(X[(2 + c) * nc + cc]);
-            Lv[2 + c] = rho_f * fmax(au, alpha1 * cs_f);
-            Rv[2 + c] = fmax(au, alpha2 * cs_f);
-        }
-        // all 2(2+ND) reciprocals with one division
-        double den[2 * (2 + ND)], inv[2 * (2 + ND)];
-#pragma unroll
-        for (int k = 0; k < 2 + ND; ++k) {
-            den[k] = Lv[k];
-            den[2 + ND + k] = Rv[k];
-        }
-        recip_all<2 * (2 + ND)>(den, inv);
-#pragma unroll
-        for (int k = 0; k < 2 + ND; ++k) {
-            long long j = k * nc + cc;
-            L[j] = Lv[k];
-            R[j] = Rv[k];
-            Linv[j] = inv[k];
-            Rinv[j] = inv[2 + ND + k];
-            double xh = X[j] * inv[2 + ND + k];
-            if (k >= 2 && is_wall_slot(G, k - 2, P)) xh = 0.0;
-            acc += xh * xh;
-        }
+        if (!scaling_cell<ND>(IntOps<true, false>(), G, X, alpha1, alpha2, L, R, Linv, Rinv, P, cc, acc))
+            acc = scaling_cell_fp64<ND>(G, X, alpha1, alpha2, L, R, Linv, Rinv, P, cc);
     }
     double s = block_sum<128>(acc, sh);
     if (thread_linear() == 0) partials[block_linear()] = s;
