@@ -276,14 +276,16 @@ def run_arm(jf, wl, precision, steps, warmup, device, stream, profile):
     return S, X0, dt, ms, stats, X
 
 
-def e2e_arm(jf, wl, precision, steps, warmup, device, stream):
+def e2e_arm(jf, wl, precision, steps, warmup, device, stream, S=None):
     """Same metric through the public API with HOST buffers: every step copies
     the state from pinned host memory to the device, steps, and copies the
     new state back.  The same warm-up steps as the device arm come first, so
-    both time the same steps of the run."""
+    both time the same steps of the run.  S: the solver to step (the device
+    arm's, as a user keeps one solver for a run), else a new one."""
     import torch
-    o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision, **OPT_OVERRIDES)
-    S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
+    if S is None:
+        o = jf.default_options(theta=wl.theta, precond=wl.precond, precision=precision, **OPT_OVERRIDES)
+        S = jf.Solver.from_workload(wl, o, device=device, stream=stream)
     host = torch.as_tensor(wl.X0, dtype=torch.float64).pin_memory()
     X = torch.empty_like(host, device=device)
     with torch.cuda.stream(stream):
@@ -978,6 +980,8 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="cells per direction")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-new-solver", action="store_true",
+                    help="end-to-end arm on a solver of its own instead of the device arm's")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the FP64 peak probe (the roofline then uses the unit-count peak)")
@@ -1094,7 +1098,8 @@ def main():
         clocks_e2e = ClockSampler(local)
         barrier(ws)
         clocks_e2e.start()
-        ms_e2e, nbytes, st_e2e = e2e_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream)
+        ms_e2e, nbytes, st_e2e = e2e_arm(jf, wl, jf.MIXED, args.steps, args.warmup, device, stream,
+                                         None if args.e2e_new_solver else S)
         barrier(ws)
         clk_e2e = clocks_e2e.stop()
         ms_e2e = max_over_ranks(ws, ms_e2e)
