@@ -31,11 +31,15 @@
 // also gives the correct infinity on overflow.
 //
 // The integer path handles normal and zero operands whose exact result is
-// normal or zero.  Everything else (subnormal operands or results,
-// infinities, NaNs, overflow before rounding) goes to a slow path that is
-// the hardware instruction itself, in a function that is never inlined so
-// that no FP64 instruction stands on the fast path, not even predicated off
-// (a predicated-off FP64 instruction still occupies the FP64 pipe).
+// normal or zero.  mul_chk / add_chk compute without a branch and clear a
+// caller's flag for everything else (subnormal operands or results,
+// infinities, NaNs, overflow before rounding): the flux kernels check the
+// flag once per evaluation and redo that evaluation on the FP64 pipe.
+// mul_rn / add_rn, single operations, take a slow path that is the hardware
+// instruction itself.  Both redo paths sit in functions that are never
+// inlined, so that no FP64 instruction stands on the fast path, not even
+// predicated off (a predicated-off FP64 instruction still occupies the FP64
+// pipe).
 //
 // The functions compile for the host as well (plain C++ on the same
 // integer steps), where tests check them bit for bit against the host's
