@@ -6,8 +6,8 @@ per direction from the boundary type) are exercised on every direction
 and in both energy forms.  Residual elementwise at 1e-9 of each field's
 maximum and normwise at 1e-10; the scaling at 1e-14; the Jacobian-free
 product at lambda = 1e-4 (above its finite-difference noise floor) at
-1e-10; one preconditioned implicit step with fixed iteration counts at the
-tolerance of the other fixed-iteration step tests."""
+1e-10; the preconditioner at 1e-10; one preconditioned implicit step with
+fixed iteration counts against the oracle's own rounding sensitivity."""
 import dataclasses
 
 import numpy as np
@@ -121,3 +121,64 @@ def test_jv_parity_with_walls(jf, cid, n, bc, form):
     Jo, do = J.jv(P, X, D.G_operator(P, X, dt), sc, v, dt, oo)
     assert delta == pytest.approx(do, rel=1e-13)
     assert _relnorm(Jv, Jo) < 1e-10, _relnorm(Jv, Jo)
+
+
+# power-of-two grids (the multigrid preconditioner needs them), walled in x
+# and in the direction of gravity (stratified problems 2 and 4)
+PC_WALL_CASES = [
+    (2, (16, 16, 1), (1, 1, 0), 2),
+    (2, (16, 8, 1), (1, 1, 0), 1),
+    (4, (8, 8, 8), (1, 1, 1), 2),
+    (4, (8, 16, 8), (1, 0, 1), 1),
+]
+
+
+@pytest.mark.parametrize("cid,n,bc,pc", PC_WALL_CASES)
+def test_precond_parity_with_walls(jf, cid, n, bc, pc):
+    """The sound-wave (pc = 1) and sound-wave + conduction (pc = 2)
+    preconditioner, two V-cycles, FP64, against the oracle's: 1e-10; the
+    normal velocity stays zero on every wall face."""
+    from oracle import precond as PC
+    wl, P, X, Xn, dt = _wall_case(cid, n, bc, 0)
+    v = torch.as_tensor(W.random_vector(wl, 5))
+    S = jf.Solver.from_workload(wl, jf.default_options(theta=wl.theta, precond=pc, mg_cycles=2))
+    w = S.precond_apply(_dev(X), dt, _dev(v))
+    oo = J.Options(precond=pc, mg_cycles=2)
+    wo = PC.apply(PC.setup(P, X, dt, oo), v, J.scaling(P, X, oo))
+    assert _relnorm(w, wo) < 1e-10, _relnorm(w, wo)
+    wc = w.detach().cpu()
+    for c in range(P.ndim):
+        if bc[c] == W.BC_WALL:
+            f = wc[(2 + c) * P.ncell:(3 + c) * P.ncell].reshape(P.shape)
+            idx = [slice(None)] * 3
+            idx[2 - c] = 0
+            assert float(f[tuple(idx)].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("cid,n,bc,pc", PC_WALL_CASES)
+def test_step_parity_fixed_iterations_with_walls(jf, cid, n, bc, pc):
+    """Two Newton iterations of eight preconditioned GMRES iterations each
+    (deterministic mode, lambda = 1e-4): the step X^{n+1} - X^n against the
+    oracle's, scaled, normwise.  At these CFL numbers (100 and 200 on grids
+    of 8 to 16 cells) the unconverged Krylov iterations amplify round-off:
+    a 1-ulp change of X^n moves the oracle's own step by 3e-8 to 8e-4
+    (measured), so the bound is a multiple of that sensitivity (and 1e-10
+    where it is smaller), as in the other fixed-iteration step tests."""
+    wl, P, X, Xn, dt = _wall_case(cid, n, bc, 0)
+    o = jf.default_options(theta=wl.theta, precond=pc, gmres_m=8, gmres_max_it=8, newton_max=2,
+                           fixed_iterations=1, lam=1e-4)
+    S = jf.Solver.from_workload(wl, o)
+    Xg = _dev(Xn)
+    st = S.step(Xg, dt)
+    assert st["newton_iterations"] == 2
+    oo = J.Options(precond=pc, gmres_m=8, gmres_max_it=8, newton_max=2, fixed_iterations=True, lam=1e-4)
+    Xo, _ = J.newton_step(P, Xn, dt, oo)
+    sc = J.scaling(P, Xn, oo)
+    err = _relnorm(Xg - _dev(Xn), Xo - Xn, sc.R)
+    sens = 0.0
+    for sd in (1, 2):
+        rng = np.random.default_rng(sd)
+        Xp = Xn * (1.0 + torch.as_tensor(rng.choice([-1.0, 1.0], Xn.numel())) * 2.0 ** -52)
+        sens = max(sens, _relnorm(J.newton_step(P, Xp, dt, oo)[0] - Xp, Xo - Xn, sc.R))
+    print("walled step %s: gpu-oracle %.2e, oracle 1-ulp sensitivity %.2e" % (bc, err, sens))
+    assert err < max(1e-10, 4.0 * sens), (err, sens)
