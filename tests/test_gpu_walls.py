@@ -6,8 +6,9 @@ per direction from the boundary type) are exercised on every direction
 and in both energy forms.  Residual elementwise at 1e-9 of each field's
 maximum and normwise at 1e-10; the scaling at 1e-14; the Jacobian-free
 product at lambda = 1e-4 (above its finite-difference noise floor) at
-1e-10; the preconditioner at 1e-10; one preconditioned implicit step with
-fixed iteration counts against the oracle's own rounding sensitivity."""
+1e-10; the preconditioner and the adjoint's J^T w at 1e-10; one
+preconditioned implicit step with fixed iteration counts against the
+oracle's own rounding sensitivity."""
 import dataclasses
 
 import numpy as np
@@ -182,3 +183,18 @@ def test_step_parity_fixed_iterations_with_walls(jf, cid, n, bc, pc):
         sens = max(sens, _relnorm(J.newton_step(P, Xp, dt, oo)[0] - Xp, Xo - Xn, sc.R))
     print("walled step %s: gpu-oracle %.2e, oracle 1-ulp sensitivity %.2e" % (bc, err, sens))
     assert err < max(1e-10, 4.0 * sens), (err, sens)
+
+
+@pytest.mark.parametrize("cid,n,bc", WALL_CASES)
+@pytest.mark.parametrize("form", [0, 1])
+def test_vjp_residual_parity_with_walls(jf, cid, n, bc, form):
+    """The transposed residual Jacobian product (the adjoint's J^T w, its
+    wall mirrors scattered back with their signs) against the oracle's
+    reverse-mode product: 1e-10."""
+    from oracle import adjoint as A
+    wl, P, X, Xn, dt = _wall_case(cid, n, bc, form)
+    w = torch.as_tensor(W.random_vector(wl, 4))
+    S = _solver(jf, wl)
+    y = S.vjp_residual(_dev(X), dt, _dev(w))
+    yo = A.vjp_G(P, X, dt, w)
+    assert _relnorm(y, yo) < 1e-10, _relnorm(y, yo)
